@@ -1,0 +1,183 @@
+"""Element integration of the coupled u / micro-equivalent-strain system.
+
+One call evaluates, for a set of elements and all their Gauss points at once
+(the whole-array style of the paper's Algorithm 2), the element blocks of the
+tangent (Eq. 11a-d) and of the residual (Eq. 11e-f, written as r = -F):
+
+  r_u   = sum_q B_u^T sigma dV,          sigma = (1 - D) C_e eps
+  r_e   = sum_q [N h (ebar - eps_eq) + B_e^T g h c grad(ebar)] dV
+  K_uu  = sum_q B_u^T (1 - D) C_e B_u dV                              (11a)
+  K_ue  = -sum_q B_u^T (C_e eps) D' chi N^T dV                         (11b)
+  K_eu  = -sum_q N h (d eps_eq/d eps)^T B_u dV                         (11c)
+  K_ee  = sum_q [h N N^T + g h c B_e^T B_e + h c g' D' chi (B_e^T grad ebar) N^T] dV  (11d)
+
+Readings: sigma carries no h-term (the paper's own element code forms
+f_u = -k_uu u_e and passes no h to its K_ue routine); the gradient term of
+F_e takes the sign that makes F_e = -r_e; dg/dkappa in Eq. 11d is
+g'(D) D'(kappa) chi.  Equal-order elements: 2-node bar, 4-node quad and
+8-node hex for both fields, with 2, 2x2, 2x2x2 Gauss points at +-1/sqrt(3).
+Gauss point q sits at the reference position of local node q scaled by
+1/sqrt(3), so Gauss-point arrays follow the node order.
+"""
+import numpy as np
+
+from . import constitutive as cm
+
+L2, Q4, H8 = 1, 2, 3
+_REF = {
+    L2: np.array([[-1.0], [1.0]]),
+    Q4: np.array([[-1.0, -1.0], [1.0, -1.0], [1.0, 1.0], [-1.0, 1.0]]),
+    H8: np.array([[-1.0, -1.0, -1.0], [1.0, -1.0, -1.0], [1.0, 1.0, -1.0], [-1.0, 1.0, -1.0],
+                  [-1.0, -1.0, 1.0], [1.0, -1.0, 1.0], [1.0, 1.0, 1.0], [-1.0, 1.0, 1.0]]),
+}
+
+
+def reference_nodes(elem):
+    return _REF[elem]
+
+
+def gauss_rule(elem):
+    """Gauss points (ngp, d) and weights (ngp,): tensor 2-point rule."""
+    xi = _REF[elem] / np.sqrt(3.0)
+    return xi, np.ones(xi.shape[0])
+
+
+def shape_functions(elem, xi):
+    """Lagrange (multi)linear shape functions and reference derivatives.
+
+    N_a(xi) = prod_i (1 + xi_i xi_a,i) / 2; returns N (np, nen) and
+    dN/dxi (np, nen, d).
+    """
+    ref = _REF[elem]
+    fac = (1.0 + xi[:, None, :] * ref[None, :, :]) / 2.0          # (np, nen, d)
+    N = np.prod(fac, axis=2)
+    d = ref.shape[1]
+    dN = np.empty(fac.shape)
+    for j in range(d):
+        others = np.prod(np.delete(fac, j, axis=2), axis=2) if d > 1 else 1.0
+        dN[:, :, j] = ref[None, :, j] / 2.0 * others
+    return N, dN
+
+
+def strain_displacement(dNdx):
+    """B_u in Voigt form (engineering shear) from physical derivatives.
+
+    dNdx: (..., nen, d) -> B: (..., nv, nen*d), dofs ordered (a, i) -> d*a + i.
+    """
+    lead = dNdx.shape[:-2]
+    nen, d = dNdx.shape[-2:]
+    nv = {1: 1, 2: 3, 3: 6}[d]
+    B = np.zeros(lead + (nv, nen * d), dtype=dNdx.dtype)
+    for a in range(nen):
+        gx = dNdx[..., a, 0]
+        if d == 1:
+            B[..., 0, a] = gx
+            continue
+        gy = dNdx[..., a, 1]
+        if d == 2:
+            B[..., 0, 2 * a] = gx
+            B[..., 1, 2 * a + 1] = gy
+            B[..., 2, 2 * a] = gy
+            B[..., 2, 2 * a + 1] = gx
+            continue
+        gz = dNdx[..., a, 2]
+        c = 3 * a
+        B[..., 0, c] = gx
+        B[..., 1, c + 1] = gy
+        B[..., 2, c + 2] = gz
+        B[..., 3, c + 1] = gz
+        B[..., 3, c + 2] = gy
+        B[..., 4, c] = gz
+        B[..., 4, c + 2] = gx
+        B[..., 5, c] = gy
+        B[..., 5, c + 1] = gx
+    return B
+
+
+def geometry(mesh, elems):
+    """Physical shape derivatives dN/dx (ne, ngp, nen, d) and dV (ne, ngp)."""
+    xi, w = gauss_rule(mesh.elem)
+    _, dN = shape_functions(mesh.elem, xi)
+    X = mesh.coords()[mesh.conn[elems]]                          # (ne, nen, d)
+    J = np.einsum("eai,qaj->eqij", X, dN)                        # dx_i/dxi_j
+    detJ = np.linalg.det(J)
+    Jinv = np.linalg.inv(J)                                      # dxi_j/dx_i = Jinv[j, i]
+    dNdx = np.einsum("qaj,eqji->eqai", dN, Jinv)
+    dV = w[None, :] * detJ * mesh.vol_scale[elems][:, None]
+    return dNdx, dV
+
+
+def element_terms(mesh, mat, u, kappa_hist, elems=None):
+    """Element tangent blocks, residual blocks and Gauss-point fields.
+
+    u: nodal dofs [ndof] (interleaved, may be complex for complex-step checks);
+    kappa_hist: committed history [nel*ngp] (real).
+    Returns a dict of arrays over the selected elements.
+    """
+    if elems is None:
+        elems = np.arange(mesh.nel)
+    elems = np.asarray(elems)
+    d, nen, nd = mesh.dim, mesh.nen, mesh.nd
+    xi, _ = gauss_rule(mesh.elem)
+    N, _ = shape_functions(mesh.elem, xi)                        # (ngp, nen)
+    dNdx, dV = geometry(mesh, elems)
+    B = strain_displacement(dNdx)                                # (ne, ngp, nv, nen*d)
+
+    U = np.asarray(u).reshape(mesh.nnode, nd)[mesh.conn[elems]]  # (ne, nen, nd)
+    ue = U[:, :, :d].reshape(len(elems), nen * d)
+    ee = U[:, :, d]                                              # (ne, nen)
+
+    C = cm.elasticity_matrix(d, mat.E, mat.nu)
+    Ce = mesh.e_scale[elems][:, None, None] * C                  # (ne, nv, nv)
+
+    eps = np.einsum("eqvk,ek->eqv", B, ue)                       # strain
+    eps_eq, deq = cm.equivalent_strain(eps, d, mat.nu, mat.k, mat.evm_variant)
+    ebar = np.einsum("qa,ea->eq", N, ee)                         # micro-equivalent strain at GP
+    gbar = np.einsum("eqai,ea->eqi", dNdx, ee)                   # its gradient
+    kh = np.asarray(kappa_hist).reshape(mesh.nel, mesh.ngp)[elems]
+    kappa, chi = cm.history(kh, ebar)
+    D, dD = cm.damage(kappa, mat.kappa0, mat.alpha, mat.beta)
+    g, dg = cm.interaction(D, mat.R, mat.eta)
+    Ceps = np.einsum("evw,eqw->eqv", Ce, eps)
+    sigma = (1.0 - D)[..., None] * Ceps
+    h, c = mat.h, mat.c
+
+    ru = np.einsum("eqvk,eqv,eq->ek", B, sigma, dV)
+    re = (np.einsum("qa,eq->ea", N, h * (ebar - eps_eq) * dV)
+          + np.einsum("eqai,eqi,eq->ea", dNdx, gbar, g * h * c * dV))
+
+    Kuu = np.einsum("eqvk,evw,eqwl,eq->ekl", B, Ce, B, (1.0 - D) * dV)
+    Kue = -np.einsum("eqvk,eqv,qb,eq->ekb", B, Ceps, N, dD * chi * dV)
+    Keu = -np.einsum("qa,eqv,eqvk,eq->eak", N, deq, B, h * dV)
+    Kee = (np.einsum("qa,qb,eq->eab", N, N, h * dV)
+           + np.einsum("eqai,eqbi,eq->eab", dNdx, dNdx, g * h * c * dV)
+           + np.einsum("eqai,eqi,qb,eq->eab", dNdx, gbar, N, h * c * dg * dD * chi * dV))
+    return dict(Kuu=Kuu, Kue=Kue, Keu=Keu, Kee=Kee, ru=ru, re=re,
+                eps=eps, eps_eq=eps_eq, ebar=ebar, gbar=gbar, kappa=kappa, chi=chi,
+                D=D, g=g, Ceps=Ceps, dV=dV)
+
+
+def local_dofs(mesh, elems):
+    """Global dof numbers of the element blocks: u part (ne, nen*d), e part (ne, nen)."""
+    conn = mesh.conn[np.asarray(elems)].astype(np.int64)
+    d, nd = mesh.dim, mesh.nd
+    gu = (nd * conn[:, :, None] + np.arange(d)[None, None, :]).reshape(conn.shape[0], -1)
+    ge = nd * conn + d
+    return gu, ge
+
+
+def element_matrix(terms):
+    """Element tangent in block order [u dofs; e dofs] (the paper's k_local)."""
+    top = np.concatenate([terms["Kuu"], terms["Kue"]], axis=2)
+    bot = np.concatenate([terms["Keu"], terms["Kee"]], axis=2)
+    return np.concatenate([top, bot], axis=1), np.concatenate([terms["ru"], terms["re"]], axis=1)
+
+
+def gp_ebar(mesh, u, elems=None):
+    """Micro-equivalent strain at every Gauss point, (ne, ngp)."""
+    if elems is None:
+        elems = np.arange(mesh.nel)
+    xi, _ = gauss_rule(mesh.elem)
+    N, _ = shape_functions(mesh.elem, xi)
+    ee = np.asarray(u).reshape(mesh.nnode, mesh.nd)[mesh.conn[elems], mesh.dim]
+    return np.einsum("qa,ea->eq", N, ee)
