@@ -1,0 +1,205 @@
+/*
+ * lgdm.h - C ABI of the GB300 library for the localizing gradient damage
+ * method (LGDM): per-Newton-iteration integration of the coupled
+ * displacement / micro-equivalent-strain system over all elements and Gauss
+ * points, deterministic assembly into a fixed CSR pattern, a preconditioned
+ * Krylov solve, the Newton update and the history commit.
+ *
+ * The calls follow the paper's statement of the problem (Algorithm 1 and 2:
+ * "Input: geometry, material properties, loads and boundary conditions;
+ * output: damage and structural response"): a mesh, a material and a set of
+ * displacement-controlled Dirichlet conditions go in; load-step, Newton-step,
+ * assemble, solve and commit calls drive the incremental-iterative procedure.
+ *
+ * Conventions used by every call
+ *   - Units: mm, N, MPa.  Scalars are double unless stated.
+ *   - Dofs are interleaved per node: dof nd*a + i with nd = dim + 1; i < dim
+ *     are displacement components, i == dim is the micro-equivalent strain.
+ *   - Gauss point q of an element sits at the reference position of its local
+ *     node q scaled by 1/sqrt(3); per-Gauss-point arrays are [nelem][ngp].
+ *   - Host pointers passed in are read during the call only (copied); the
+ *     caller keeps ownership.  Device memory is never allocated by the
+ *     library: the caller passes one device workspace (sized by
+ *     lgdm_workspace_size) and a CUDA stream, both caller-owned and required
+ *     to outlive the simulation handle.
+ *   - Kernels run on the caller's stream.  Calls that return host scalars
+ *     synchronise that stream only; the others are asynchronous.
+ *   - Every call returns an lgdm_status; on failure a message is available
+ *     from lgdm_last_error().  No C++ exception crosses this boundary.
+ *   - A handle is not thread-safe: one host thread drives one handle at a time.
+ */
+#ifndef LGDM_H
+#define LGDM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LGDM_ABI_VERSION 1
+
+typedef enum {
+  LGDM_OK = 0,
+  LGDM_ERR_INVALID_ARG = 1,   /* bad pointer, size or option                   */
+  LGDM_ERR_OOM = 2,           /* workspace smaller than lgdm_workspace_size()  */
+  LGDM_ERR_CUDA = 3,          /* a CUDA runtime call failed                    */
+  LGDM_ERR_NOT_CONVERGED = 4, /* Newton failed after all increment halvings    */
+  LGDM_ERR_NONFINITE = 5,     /* NaN/Inf met in the solve or the update        */
+  LGDM_ERR_TIMEOUT = 6,       /* a bounded device-side wait gave up            */
+  LGDM_ERR_STATE = 7          /* call out of order                             */
+} lgdm_status;
+
+typedef enum { LGDM_L2 = 1, LGDM_Q4 = 2, LGDM_H8 = 3 } lgdm_elem;
+
+/* Arithmetic of the tangent.  FP64: everything in double.  FP32_TANGENT: the
+ * element tangent, the CSR values, the SpMV and the preconditioner in float
+ * (an inexact-Newton matrix); residual, Krylov vectors, inner products, the
+ * update and the convergence test stay double. */
+typedef enum { LGDM_PREC_FP64 = 0, LGDM_PREC_FP32_TANGENT = 1 } lgdm_precision;
+
+typedef enum { LGDM_PRECOND_JACOBI = 0, LGDM_PRECOND_NODE_BLOCK = 1 } lgdm_precond;
+
+typedef enum {
+  LGDM_FIELD_U = 0,          /* [ndof]  current nodal dofs (interleaved)         */
+  LGDM_FIELD_KAPPA_HIST = 1, /* [nelem*ngp] committed history (Eq. A.2)          */
+  LGDM_FIELD_DAMAGE = 2,     /* [nelem*ngp] D(kappa_hist) (Eq. A.1)              */
+  LGDM_FIELD_DELTA = 3,      /* [ndof]  last Newton increment from lgdm_solve    */
+  LGDM_FIELD_RESIDUAL = 4,   /* [ndof]  last assembled r = -F before Dirichlet rows */
+  LGDM_FIELD_RHS = 5         /* [ndof]  -r with zeros on Dirichlet dofs          */
+} lgdm_field;
+
+/* Mesh: equal-order elements, 2 / 2x2 / 2x2x2 Gauss points (Sec. 2.2; the
+ * element types of the benchmark configurations).  Local node order: bar
+ * left->right; quad counter-clockwise from (-1,-1); hex bottom face
+ * counter-clockwise then top face. */
+typedef struct {
+  int32_t elem;               /* lgdm_elem                                        */
+  int32_t nnode, nelem;
+  const double *x, *y, *z;    /* [nnode] coordinates; y, z NULL when unused       */
+  const int32_t *conn;        /* [nelem*nen] element-major connectivity           */
+  const double *e_scale;      /* [nelem] multiplies the elasticity only; NULL = 1 */
+  const double *vol_scale;    /* [nelem] multiplies dV (bar area); NULL = 1       */
+} lgdm_mesh;
+
+/* Material (Sec. 2.1, Appendix A).  eta is the exponent "n" of Eq. A.4.
+ * evm_variant 0 uses 12k/(1+nu)^2 in front of J2 = dev(eps):dev(eps)/2 in
+ * Eq. A.3 (uniaxial stress gives eps_eq = axial strain); 1 uses the printed
+ * 2k/(1-nu)^2.  In 1D eps_eq is the axial strain and nu, k are ignored. */
+typedef struct {
+  double E, nu, k, kappa0, alpha, beta, R, eta, c, h;
+  int32_t evm_variant;
+} lgdm_material;
+
+/* Displacement control: u[dir_dof[i]] = dir_scale[i] * load at each load
+ * step.  The reaction is sum_i dir_scale[i] * r[dir_dof[i]]. */
+typedef struct {
+  int32_t n_dir;
+  const int32_t *dir_dof;
+  const double *dir_scale;
+} lgdm_bcs;
+
+typedef struct {
+  int32_t precision;          /* lgdm_precision                                   */
+  int32_t precond;            /* lgdm_precond                                     */
+  double newton_tol;          /* ||du|| <= tol ||u|| and ||de|| <= tol ||e||      */
+  double krylov_rtol;         /* BiCGSTAB stop: ||r|| <= rtol ||b||               */
+  int32_t max_newton;         /* Newton iterations per attempt                    */
+  int32_t max_krylov;         /* BiCGSTAB iterations per solve                    */
+  int32_t max_halvings;       /* load-increment halvings before giving up         */
+  int32_t krylov_blocks;      /* 0 = as many co-resident blocks as fit            */
+} lgdm_options;
+
+typedef struct lgdm_sim lgdm_sim;
+
+/* Sizes of a created simulation. */
+typedef struct {
+  int32_t dim, nen, ngp, nd;
+  int32_t nnode, nelem;
+  int64_t ndof, nnz, npairs;  /* npairs: node pairs sharing an element */
+  size_t workspace_bytes;
+} lgdm_sizes;
+
+int32_t lgdm_abi_version(void);
+const char *lgdm_status_string(lgdm_status s);
+
+/* Fill *opt with the defaults (FP64, node-block Jacobi, tol 1e-8, rtol 1e-8,
+ * 50 Newton iterations, 5000 Krylov iterations, 6 halvings). */
+lgdm_status lgdm_default_options(lgdm_options *opt);
+
+/* Device workspace bytes the simulation of this mesh needs.  Builds the node
+ * adjacency on the host to count the CSR pattern exactly. */
+lgdm_status lgdm_workspace_size(const lgdm_mesh *mesh, const lgdm_options *opt, size_t *bytes);
+
+/* Create a simulation.  Copies the mesh, material and conditions, builds the
+ * node-block CSR pattern and the element-to-nonzero map on the host, uploads
+ * them into dev_workspace (>= lgdm_workspace_size bytes, 256-byte aligned)
+ * on `stream` (a cudaStream_t; NULL = the default stream), and sets the
+ * initial state u = 0, kappa_hist = kappa0 (Eq. A.1-A.2). */
+lgdm_status lgdm_create(const lgdm_mesh *mesh, const lgdm_material *mat, const lgdm_bcs *bcs,
+                        const lgdm_options *opt, void *dev_workspace, size_t workspace_bytes,
+                        void *stream, lgdm_sim **out);
+void lgdm_destroy(lgdm_sim *sim);
+const char *lgdm_last_error(const lgdm_sim *sim);
+lgdm_status lgdm_get_sizes(const lgdm_sim *sim, lgdm_sizes *out);
+
+/* Replace the state from host arrays u [ndof] and kappa_hist [nelem*ngp]
+ * (either may be NULL to keep it).  The result is also the committed state. */
+lgdm_status lgdm_set_state(lgdm_sim *sim, const double *u, const double *kappa_hist);
+
+/* Copy a field (lgdm_field) into host memory of n doubles (n must match). */
+lgdm_status lgdm_get_field(lgdm_sim *sim, int32_t which, double *host_dst, size_t n);
+
+/* Start a load step (Algorithm 2, line 2): set the Dirichlet dofs of the
+ * committed state to dir_scale * load. */
+lgdm_status lgdm_begin_step(lgdm_sim *sim, double load);
+
+/* Compute and assemble K and F at the current state (Algorithm 2, lines
+ * 6-7; Eq. 11a-f): element integration over every Gauss point, deterministic
+ * summation into the CSR values and the residual (no float atomics; the
+ * summation order is fixed by the mesh alone), identity rows and zero
+ * columns on Dirichlet dofs.  Asynchronous. */
+lgdm_status lgdm_assemble(lgdm_sim *sim);
+
+/* Copy the assembled system to the host: rowptr [ndof+1], col [nnz],
+ * vals [nnz] (as double in either precision), rhs [ndof] (= F with zeros on
+ * Dirichlet dofs).  Any pointer may be NULL to skip it. */
+lgdm_status lgdm_get_system(lgdm_sim *sim, int32_t *rowptr, int32_t *col, double *vals, double *rhs);
+
+/* Solve K delta = F (Algorithm 2, line 8) with BiCGSTAB preconditioned by the
+ * chosen Jacobi variant, one persistent launch; delta is kept on the device
+ * (LGDM_FIELD_DELTA).  Synchronises; iters / rel_res may be NULL. */
+lgdm_status lgdm_solve(lgdm_sim *sim, int32_t *iters, double *rel_res);
+
+/* u += delta and the convergence test of Algorithm 2, line 18.  Synchronises. */
+lgdm_status lgdm_update(lgdm_sim *sim, int32_t *converged);
+
+/* One Newton iteration: assemble, then one persistent launch that solves,
+ * updates and tests convergence.  Synchronises once. */
+lgdm_status lgdm_newton_step(lgdm_sim *sim, int32_t *converged, int32_t *krylov_iters);
+
+/* One load step to `load`: begin_step, Newton iterations until convergence,
+ * commit; on non-convergence the increment is halved and retried from the
+ * committed state, up to max_halvings times.  newton_iters (may be NULL)
+ * receives the total number of Newton iterations spent. */
+lgdm_status lgdm_run_step(lgdm_sim *sim, double load, int32_t *newton_iters);
+
+/* History commit after convergence (Eq. A.2): kappa_hist <- max(kappa_hist,
+ * ebar at every Gauss point); the current u becomes the committed state and
+ * the reaction at this converged state is evaluated on the device. */
+lgdm_status lgdm_commit(lgdm_sim *sim);
+
+/* Statistics of the last Krylov launch (lgdm_solve, lgdm_update or
+ * lgdm_newton_step): iterations, status (0 converged, 1 iteration limit,
+ * 2 breakdown, 3 non-finite, 4 barrier timeout), relative residual, and the
+ * norms ||du||, ||u||, ||de||, ||e|| of the last update (norms4 may be NULL). */
+lgdm_status lgdm_last_solve(lgdm_sim *sim, int32_t *iters, int32_t *status, double *rel_res, double *norms4);
+
+/* Reaction at the last committed state.  Synchronises. */
+lgdm_status lgdm_get_reaction(lgdm_sim *sim, double *reaction);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LGDM_H */

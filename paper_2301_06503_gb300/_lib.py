@@ -1,0 +1,110 @@
+"""ctypes declarations of the LGDM C ABI (include/lgdm.h).
+
+Argument marshalling only.  Loading fails loudly when the compiled library is
+absent: there is no CPU fallback for any call.
+"""
+import ctypes as C
+import os
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "liblgdm.so")
+
+L2, Q4, H8 = 1, 2, 3
+PREC_FP64, PREC_FP32_TANGENT = 0, 1
+PRECOND_JACOBI, PRECOND_NODE_BLOCK = 0, 1
+FIELD_U, FIELD_KAPPA_HIST, FIELD_DAMAGE, FIELD_DELTA, FIELD_RESIDUAL, FIELD_RHS = range(6)
+STATUS = {0: "ok", 1: "invalid argument", 2: "workspace too small", 3: "CUDA error",
+          4: "Newton did not converge", 5: "non-finite value", 6: "device wait timed out",
+          7: "call out of order"}
+
+_dp = C.POINTER(C.c_double)
+_ip = C.POINTER(C.c_int32)
+
+
+class Mesh(C.Structure):
+    _fields_ = [("elem", C.c_int32), ("nnode", C.c_int32), ("nelem", C.c_int32),
+                ("x", _dp), ("y", _dp), ("z", _dp), ("conn", _ip),
+                ("e_scale", _dp), ("vol_scale", _dp)]
+
+
+class Material(C.Structure):
+    _fields_ = [(n, C.c_double) for n in ("E", "nu", "k", "kappa0", "alpha", "beta", "R", "eta", "c", "h")] + \
+               [("evm_variant", C.c_int32)]
+
+
+class BCs(C.Structure):
+    _fields_ = [("n_dir", C.c_int32), ("dir_dof", _ip), ("dir_scale", _dp)]
+
+
+class Options(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("precond", C.c_int32), ("newton_tol", C.c_double),
+                ("krylov_rtol", C.c_double), ("max_newton", C.c_int32), ("max_krylov", C.c_int32),
+                ("max_halvings", C.c_int32), ("krylov_blocks", C.c_int32)]
+
+
+class Sizes(C.Structure):
+    _fields_ = [("dim", C.c_int32), ("nen", C.c_int32), ("ngp", C.c_int32), ("nd", C.c_int32),
+                ("nnode", C.c_int32), ("nelem", C.c_int32), ("ndof", C.c_int64), ("nnz", C.c_int64),
+                ("npairs", C.c_int64), ("workspace_bytes", C.c_size_t)]
+
+
+class LgdmError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+_SIGS = {
+    "lgdm_abi_version": (C.c_int32, []),
+    "lgdm_status_string": (C.c_char_p, [C.c_int]),
+    "lgdm_default_options": (C.c_int, [C.POINTER(Options)]),
+    "lgdm_workspace_size": (C.c_int, [C.POINTER(Mesh), C.POINTER(Options), C.POINTER(C.c_size_t)]),
+    "lgdm_create": (C.c_int, [C.POINTER(Mesh), C.POINTER(Material), C.POINTER(BCs), C.POINTER(Options),
+                              C.c_void_p, C.c_size_t, C.c_void_p, C.POINTER(C.c_void_p)]),
+    "lgdm_destroy": (None, [C.c_void_p]),
+    "lgdm_last_error": (C.c_char_p, [C.c_void_p]),
+    "lgdm_get_sizes": (C.c_int, [C.c_void_p, C.POINTER(Sizes)]),
+    "lgdm_set_state": (C.c_int, [C.c_void_p, _dp, _dp]),
+    "lgdm_get_field": (C.c_int, [C.c_void_p, C.c_int32, _dp, C.c_size_t]),
+    "lgdm_begin_step": (C.c_int, [C.c_void_p, C.c_double]),
+    "lgdm_assemble": (C.c_int, [C.c_void_p]),
+    "lgdm_get_system": (C.c_int, [C.c_void_p, _ip, _ip, _dp, _dp]),
+    "lgdm_solve": (C.c_int, [C.c_void_p, _ip, _dp]),
+    "lgdm_update": (C.c_int, [C.c_void_p, _ip]),
+    "lgdm_newton_step": (C.c_int, [C.c_void_p, _ip, _ip]),
+    "lgdm_run_step": (C.c_int, [C.c_void_p, C.c_double, _ip]),
+    "lgdm_commit": (C.c_int, [C.c_void_p]),
+    "lgdm_last_solve": (C.c_int, [C.c_void_p, _ip, _ip, _dp, _dp]),
+    "lgdm_get_reaction": (C.c_int, [C.c_void_p, _dp]),
+}
+
+_lib = None
+
+
+def load(path: str = LIB_PATH) -> C.CDLL:
+    """Load liblgdm.so and declare every ABI function (raises if it is missing)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"LGDM CUDA library not built ({path} missing); run "
+                           "paper_2301_06503_gb300.build.build() or __graft_entry__.build()")
+    lib = C.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    if lib.lgdm_abi_version() != 1:
+        raise RuntimeError("LGDM ABI version mismatch")
+    _lib = lib
+    return lib
+
+
+def abi_names():
+    return list(_SIGS)
+
+
+def check(status: int, handle=None) -> None:
+    if status != 0:
+        msg = load().lgdm_last_error(handle)
+        raise LgdmError(status, msg.decode() if msg else "")

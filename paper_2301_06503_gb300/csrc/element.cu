@@ -1,0 +1,675 @@
+// Element integration and deterministic assembly of the LGDM coupled system.
+//
+// element_kernel: one team of NEN threads per element (NEN = NGP for the
+// 2-node bar, 4-node quad and 8-node hex with 2/2x2/2x2x2 Gauss rules).
+//   Phase 1: thread q evaluates Gauss point q of its element: Jacobian,
+//     shape derivatives, strain (B_u u), micro-equivalent strain and its
+//     gradient, modified von Mises equivalent strain and gradient (Eq. A.3),
+//     trial history kappa = max(kappa_hist, ebar) (Eq. A.2), damage D and
+//     dD/dkappa (Eq. A.1), interaction g and dg/dD (Eq. A.4), stresses
+//     (Eq. 2 without its h-term, Eq. 3-4), and stores the per-point factors
+//     the element matrices need in shared memory.
+//   Phase 2: thread a forms block row a of the element tangent (Eq. 11a-d)
+//     and of the residual r = -F (Eq. 11e-f) by summing over the Gauss
+//     points; the element matrix goes to a scratch buffer in node-block
+//     layout Ke[e][a][i][b][j].
+// gather_kernel: one thread per node pair (a, b) sums the nd x nd blocks of
+//   every element containing both nodes, in the fixed order of a
+//   precomputed contribution list (no float atomics), applies identity
+//   rows / zero columns on Dirichlet dofs and writes the CSR values; the
+//   diagonal pairs also sum the residual.
+#include "lgdm_internal.cuh"
+#include <cmath>
+
+namespace lgdm {
+
+MatConst make_matconst(const lgdm_material &m, int dim) {
+  MatConst c{};
+  if (dim == 1) {
+    c.lam = m.E;
+    c.mu = 0.0;
+  } else {
+    c.lam = m.E * m.nu / ((1.0 + m.nu) * (1.0 - 2.0 * m.nu));
+    c.mu = m.E / (2.0 * (1.0 + m.nu));
+  }
+  c.evm_a = (m.k - 1.0) / (2.0 * m.k * (1.0 - 2.0 * m.nu));
+  const double b = (m.k - 1.0) / (1.0 - 2.0 * m.nu);
+  c.evm_b2 = b * b;
+  c.evm_cJ = (m.evm_variant == 0) ? 12.0 * m.k / ((1.0 + m.nu) * (1.0 + m.nu))
+                                  : 2.0 * m.k / ((1.0 - m.nu) * (1.0 - m.nu));
+  c.inv2k = 1.0 / (2.0 * m.k);
+  c.kappa0 = m.kappa0;
+  c.alpha = m.alpha;
+  c.beta = m.beta;
+  const double en = std::exp(-m.eta);
+  c.g_a = (1.0 - m.R) / (1.0 - en);
+  c.g_b = (m.R - en) / (1.0 - en);
+  c.eta = m.eta;
+  c.h = m.h;
+  c.c = m.c;
+  return c;
+}
+
+// ------------------------------------------------------------------ helpers
+// B_b^T v for a Voigt vector v (engineering shear), physical derivatives g.
+template <int DIM, typename T>
+__device__ __forceinline__ void BtV(const T *g, const T *v, T *out) {
+  if constexpr (DIM == 1) {
+    out[0] = g[0] * v[0];
+  } else if constexpr (DIM == 2) {
+    out[0] = g[0] * v[0] + g[1] * v[2];
+    out[1] = g[1] * v[1] + g[0] * v[2];
+  } else {
+    out[0] = g[0] * v[0] + g[1] * v[5] + g[2] * v[4];
+    out[1] = g[1] * v[1] + g[0] * v[5] + g[2] * v[3];
+    out[2] = g[2] * v[2] + g[1] * v[3] + g[0] * v[4];
+  }
+}
+
+// Isotropic C eps (Voigt, engineering shear).  In 1D lam holds E.
+template <int DIM>
+__device__ __forceinline__ void iso_stress(double lam, double mu, const double *e, double *s) {
+  if constexpr (DIM == 1) {
+    s[0] = lam * e[0];
+  } else if constexpr (DIM == 2) {
+    const double tr = e[0] + e[1];
+    s[0] = lam * tr + 2.0 * mu * e[0];
+    s[1] = lam * tr + 2.0 * mu * e[1];
+    s[2] = mu * e[2];
+  } else {
+    const double tr = e[0] + e[1] + e[2];
+    s[0] = lam * tr + 2.0 * mu * e[0];
+    s[1] = lam * tr + 2.0 * mu * e[1];
+    s[2] = lam * tr + 2.0 * mu * e[2];
+    s[3] = mu * e[3];
+    s[4] = mu * e[4];
+    s[5] = mu * e[5];
+  }
+}
+
+// Modified von Mises equivalent strain (Eq. A.3) and its Voigt gradient.
+template <int DIM>
+__device__ __forceinline__ double equivalent_strain(const MatConst &mc, const double *e, double *d) {
+  if constexpr (DIM == 1) {
+    d[0] = 1.0;
+    return e[0];
+  } else {
+    constexpr int NV = (DIM == 2) ? 3 : 6;
+    double I1, ee;
+    if constexpr (DIM == 2) {
+      I1 = e[0] + e[1];
+      ee = e[0] * e[0] + e[1] * e[1] + 0.5 * e[2] * e[2];
+    } else {
+      I1 = e[0] + e[1] + e[2];
+      ee = e[0] * e[0] + e[1] * e[1] + e[2] * e[2] + 0.5 * (e[3] * e[3] + e[4] * e[4] + e[5] * e[5]);
+    }
+    const double J2 = 0.5 * (ee - I1 * I1 * (1.0 / 3.0));
+    const double Q = mc.evm_b2 * I1 * I1 + mc.evm_cJ * J2;
+    if (Q > 0.0) {
+      const double root = sqrt(Q);
+      const double coef = 0.5 * mc.inv2k / root;
+      const double nrm = mc.evm_a + coef * 2.0 * mc.evm_b2 * I1;   // common normal part
+      const double third = I1 * (1.0 / 3.0);
+#pragma unroll
+      for (int i = 0; i < DIM; ++i) d[i] = nrm + coef * mc.evm_cJ * (e[i] - third);
+#pragma unroll
+      for (int i = DIM; i < NV; ++i) d[i] = coef * mc.evm_cJ * 0.5 * e[i];
+      return mc.evm_a * I1 + root * mc.inv2k;
+    }
+#pragma unroll
+    for (int i = 0; i < DIM; ++i) d[i] = mc.evm_a;
+#pragma unroll
+    for (int i = DIM; i < NV; ++i) d[i] = 0.0;
+    return mc.evm_a * I1;
+  }
+}
+
+// ------------------------------------------------------------------ element kernel
+constexpr int ELEM_THREADS = 128;
+
+template <int ELEM, typename TT>
+struct ElemLayout {
+  static constexpr int DIM = Elem<ELEM>::DIM, NEN = Elem<ELEM>::NEN, NV = Elem<ELEM>::NV;
+  static constexpr int ND = DIM + 1, NGP = NEN, EPB = ELEM_THREADS / NEN;
+  // double record per Gauss point: dNdx[NEN][DIM], sig dV[NV], rho2, rho4, gbar[DIM]
+  static constexpr int RD = NEN * DIM + NV + 2 + DIM;
+  static constexpr int O_DN = 0, O_SIG = NEN * DIM, O_R2 = O_SIG + NV, O_R4 = O_R2 + 1, O_GB = O_R4 + 1;
+  // tangent record per Gauss point (TT): dNdx[NEN][DIM], z[NEN][DIM], lam', mu', s[NV], rho1, rho2, rho3, gbar[DIM]
+  static constexpr int RT = 2 * NEN * DIM + 2 + NV + 3 + DIM;
+  static constexpr int T_DN = 0, T_Z = NEN * DIM, T_LAM = 2 * NEN * DIM, T_MU = T_LAM + 1, T_S = T_MU + 1,
+                       T_R1 = T_S + NV, T_R2 = T_R1 + 1, T_R3 = T_R2 + 1, T_GB = T_R3 + 1;
+  static constexpr int RDS = (NGP * RD) | 1;                // odd stride: fewer bank conflicts
+  static constexpr int RTS = (NGP * RT) | 1;
+  static constexpr size_t BYTES_D = sizeof(double) *
+      (size_t)(NGP * NEN + NGP * NEN * DIM + EPB * NEN * DIM + EPB * NEN * ND + EPB * RDS);
+  static constexpr size_t bytes(bool res_only) {
+    return BYTES_D + (res_only ? 0 : sizeof(TT) * (size_t)(EPB * RTS));
+  }
+};
+
+template <int ELEM, typename TT, bool RES_ONLY>
+__global__ void __launch_bounds__(ELEM_THREADS)
+element_kernel(MeshView m, MatConst mc, const double *__restrict__ u, const double *__restrict__ kh,
+               const int32_t *__restrict__ elem_list, int32_t n_elem, TT *__restrict__ Ke,
+               double *__restrict__ re) {
+  using L = ElemLayout<ELEM, TT>;
+  constexpr int DIM = L::DIM, NEN = L::NEN, NV = L::NV, ND = L::ND, NGP = L::NGP, EPB = L::EPB;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double *sN = reinterpret_cast<double *>(smem_raw);            // [NGP][NEN]
+  double *sdN = sN + NGP * NEN;                                  // [NGP][NEN][DIM]
+  double *xs = sdN + NGP * NEN * DIM;                            // [EPB][NEN][DIM]
+  double *us = xs + EPB * NEN * DIM;                             // [EPB][NEN][ND]
+  double *recD = us + EPB * NEN * ND;                            // [EPB][RDS]
+  TT *recT = reinterpret_cast<TT *>(recD + EPB * L::RDS);        // [EPB][RTS]
+
+  const int tid = threadIdx.x;
+  const int el = tid / NEN, a = tid % NEN;
+  const int64_t slot = (int64_t)blockIdx.x * EPB + el;           // position in the element list
+  const bool valid = slot < n_elem;
+  const int32_t e = valid ? (elem_list ? elem_list[slot] : (int32_t)slot) : 0;
+
+  for (int k = tid; k < NGP * NEN; k += ELEM_THREADS) sN[k] = shape_N<DIM>(k / NEN, k % NEN);
+  for (int k = tid; k < NGP * NEN * DIM; k += ELEM_THREADS)
+    sdN[k] = shape_dN<DIM>(k / (NEN * DIM), (k / DIM) % NEN, k % DIM);
+  if (valid) {
+    const int32_t node = m.conn[(int64_t)e * NEN + a];
+    xs[(el * NEN + a) * DIM + 0] = m.x[node];
+    if constexpr (DIM > 1) xs[(el * NEN + a) * DIM + 1] = m.y[node];
+    if constexpr (DIM > 2) xs[(el * NEN + a) * DIM + 2] = m.z[node];
+#pragma unroll
+    for (int i = 0; i < ND; ++i) us[(el * NEN + a) * ND + i] = u[(int64_t)node * ND + i];
+  }
+  __syncthreads();
+
+  // ---------------- phase 1: Gauss point q = a
+  if (valid) {
+    const int q = a;
+    const double *X = xs + el * NEN * DIM;
+    const double *U = us + el * NEN * ND;
+    double J[DIM][DIM];
+#pragma unroll
+    for (int i = 0; i < DIM; ++i)
+#pragma unroll
+      for (int j = 0; j < DIM; ++j) {
+        double s = 0.0;
+#pragma unroll
+        for (int b = 0; b < NEN; ++b) s += X[b * DIM + i] * sdN[(q * NEN + b) * DIM + j];
+        J[i][j] = s;
+      }
+    double Ji[DIM][DIM], det;
+    if constexpr (DIM == 1) {
+      det = J[0][0];
+      Ji[0][0] = 1.0 / det;
+    } else if constexpr (DIM == 2) {
+      det = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+      const double id = 1.0 / det;
+      Ji[0][0] = J[1][1] * id;
+      Ji[0][1] = -J[0][1] * id;
+      Ji[1][0] = -J[1][0] * id;
+      Ji[1][1] = J[0][0] * id;
+    } else {
+      const double c00 = J[1][1] * J[2][2] - J[1][2] * J[2][1];
+      const double c01 = J[1][2] * J[2][0] - J[1][0] * J[2][2];
+      const double c02 = J[1][0] * J[2][1] - J[1][1] * J[2][0];
+      det = J[0][0] * c00 + J[0][1] * c01 + J[0][2] * c02;
+      const double id = 1.0 / det;
+      Ji[0][0] = c00 * id;
+      Ji[1][0] = c01 * id;
+      Ji[2][0] = c02 * id;
+      Ji[0][1] = (J[0][2] * J[2][1] - J[0][1] * J[2][2]) * id;
+      Ji[1][1] = (J[0][0] * J[2][2] - J[0][2] * J[2][0]) * id;
+      Ji[2][1] = (J[0][1] * J[2][0] - J[0][0] * J[2][1]) * id;
+      Ji[0][2] = (J[0][1] * J[1][2] - J[0][2] * J[1][1]) * id;
+      Ji[1][2] = (J[0][2] * J[1][0] - J[0][0] * J[1][2]) * id;
+      Ji[2][2] = (J[0][0] * J[1][1] - J[0][1] * J[1][0]) * id;
+    }
+    const double dV = det * m.vol_scale[e];
+    // physical derivatives dN_b/dx_i = sum_j dN_b/dxi_j dxi_j/dx_i
+    double g[NEN][DIM];
+#pragma unroll
+    for (int b = 0; b < NEN; ++b)
+#pragma unroll
+      for (int i = 0; i < DIM; ++i) {
+        double s = 0.0;
+#pragma unroll
+        for (int j = 0; j < DIM; ++j) s += sdN[(q * NEN + b) * DIM + j] * Ji[j][i];
+        g[b][i] = s;
+      }
+    // strain eps = sum_b B_b u_b (Voigt, engineering shear)
+    double eps[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) eps[v] = 0.0;
+    double eb = 0.0, gb[DIM];
+#pragma unroll
+    for (int i = 0; i < DIM; ++i) gb[i] = 0.0;
+#pragma unroll
+    for (int b = 0; b < NEN; ++b) {
+      const double *ub = U + b * ND;
+#pragma unroll
+      for (int i = 0; i < DIM; ++i) eps[i] += g[b][i] * ub[i];
+      if constexpr (DIM == 2) eps[2] += g[b][1] * ub[0] + g[b][0] * ub[1];
+      if constexpr (DIM == 3) {
+        eps[3] += g[b][2] * ub[1] + g[b][1] * ub[2];
+        eps[4] += g[b][2] * ub[0] + g[b][0] * ub[2];
+        eps[5] += g[b][1] * ub[0] + g[b][0] * ub[1];
+      }
+      eb += sN[q * NEN + b] * ub[DIM];
+#pragma unroll
+      for (int i = 0; i < DIM; ++i) gb[i] += g[b][i] * ub[DIM];
+    }
+    double deq[NV];
+    const double eq = equivalent_strain<DIM>(mc, eps, deq);
+    // trial history (Eq. A.2) and damage (Eq. A.1)
+    const double khq = kh[(int64_t)e * NGP + q];
+    const bool chi = eb > khq;
+    const double kap = chi ? eb : khq;
+    double D = 0.0, dD = 0.0;
+    if (kap > mc.kappa0) {
+      const double ex = exp(-mc.beta * (kap - mc.kappa0));
+      const double soft = 1.0 - mc.alpha + mc.alpha * ex;
+      const double rk = mc.kappa0 / kap;
+      D = 1.0 - rk * soft;
+      dD = rk / kap * soft + rk * mc.alpha * mc.beta * ex;
+    }
+    // interaction (Eq. A.4)
+    double gi = 1.0, dgi = -mc.eta * mc.g_a;
+    if (D > 0.0) {
+      const double en = exp(-mc.eta * D);
+      gi = mc.g_a * en + mc.g_b;
+      dgi = -mc.eta * mc.g_a * en;
+    }
+    const double es = m.e_scale[e];
+    double ce[NV];
+    iso_stress<DIM>(es * mc.lam, es * mc.mu, eps, ce);
+    const double omD = 1.0 - D;
+    double *rd = recD + el * L::RDS + q * L::RD;
+#pragma unroll
+    for (int b = 0; b < NEN; ++b)
+#pragma unroll
+      for (int i = 0; i < DIM; ++i) rd[L::O_DN + b * DIM + i] = g[b][i];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) rd[L::O_SIG + v] = omD * dV * ce[v];
+    const double hdV = mc.h * dV;
+    rd[L::O_R2] = gi * mc.h * mc.c * dV;
+    rd[L::O_R4] = hdV * (eb - eq);
+#pragma unroll
+    for (int i = 0; i < DIM; ++i) rd[L::O_GB + i] = gb[i];
+    if constexpr (!RES_ONLY) {
+      TT *rt = recT + el * L::RTS + q * L::RT;
+      const double lin = (chi ? dD : 0.0) * dV;      // D' chi dV
+      double tv[NV];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) tv[v] = hdV * deq[v];
+#pragma unroll
+      for (int b = 0; b < NEN; ++b) {
+        double z[DIM];
+        BtV<DIM, double>(g[b], tv, z);
+#pragma unroll
+        for (int i = 0; i < DIM; ++i) {
+          rt[L::T_DN + b * DIM + i] = (TT)g[b][i];
+          rt[L::T_Z + b * DIM + i] = (TT)z[i];
+        }
+      }
+      rt[L::T_LAM] = (TT)(omD * es * mc.lam * dV);
+      rt[L::T_MU] = (TT)(omD * es * mc.mu * dV);
+#pragma unroll
+      for (int v = 0; v < NV; ++v) rt[L::T_S + v] = (TT)(ce[v] * lin);
+      rt[L::T_R1] = (TT)hdV;
+      rt[L::T_R2] = (TT)(gi * mc.h * mc.c * dV);
+      rt[L::T_R3] = (TT)(mc.h * mc.c * dgi * lin);
+#pragma unroll
+      for (int i = 0; i < DIM; ++i) rt[L::T_GB + i] = (TT)gb[i];
+    }
+  }
+  __syncthreads();
+  if (!valid) return;
+
+  // ---------------- phase 2: block row a
+  const double *RD0 = recD + el * L::RDS;
+  {
+    double ru[DIM], rep = 0.0;
+#pragma unroll
+    for (int i = 0; i < DIM; ++i) ru[i] = 0.0;
+#pragma unroll
+    for (int q = 0; q < NGP; ++q) {
+      const double *rd = RD0 + q * L::RD;
+      const double *A = rd + L::O_DN + a * DIM;
+      double t[DIM];
+      BtV<DIM, double>(A, rd + L::O_SIG, t);
+#pragma unroll
+      for (int i = 0; i < DIM; ++i) ru[i] += t[i];
+      double ag = 0.0;
+#pragma unroll
+      for (int i = 0; i < DIM; ++i) ag += A[i] * rd[L::O_GB + i];
+      rep += sN[q * NEN + a] * rd[L::O_R4] + rd[L::O_R2] * ag;
+    }
+    double *rout = re + ((int64_t)slot * NEN + a) * ND;
+#pragma unroll
+    for (int i = 0; i < DIM; ++i) rout[i] = ru[i];
+    rout[DIM] = rep;
+  }
+  if constexpr (!RES_ONLY) {
+    const TT *RT0 = recT + el * L::RTS;
+    constexpr int BC = (NEN > 4) ? 4 : NEN;     // b columns per pass (register budget)
+#pragma unroll 1
+    for (int b0 = 0; b0 < NEN; b0 += BC) {
+      TT acc[ND][BC][ND];
+#pragma unroll
+      for (int i = 0; i < ND; ++i)
+#pragma unroll
+        for (int bb = 0; bb < BC; ++bb)
+#pragma unroll
+          for (int j = 0; j < ND; ++j) acc[i][bb][j] = (TT)0;
+#pragma unroll
+      for (int q = 0; q < NGP; ++q) {
+        const TT *rt = RT0 + q * L::RT;
+        TT A[DIM];
+#pragma unroll
+        for (int i = 0; i < DIM; ++i) A[i] = rt[L::T_DN + a * DIM + i];
+        const TT lamp = rt[L::T_LAM], mup = rt[L::T_MU];
+        const TT Na = (TT)sN[q * NEN + a];
+        TT la[DIM], ma[DIM], l2m[DIM], w[DIM], fa[DIM];
+        TT ag = (TT)0;
+#pragma unroll
+        for (int i = 0; i < DIM; ++i) {
+          la[i] = lamp * A[i];
+          ma[i] = mup * A[i];
+          l2m[i] = la[i] + (TT)2 * ma[i];
+          fa[i] = rt[L::T_R2] * A[i];
+          ag += A[i] * rt[L::T_GB + i];
+        }
+        BtV<DIM, TT>(A, rt + L::T_S, w);               // B_a^T (C eps) D' chi dV
+        const TT ea = Na * rt[L::T_R1] + rt[L::T_R3] * ag;
+        const TT nNa = -Na;
+#pragma unroll
+        for (int bb = 0; bb < BC; ++bb) {
+          const int b = b0 + bb;
+          const TT *B = rt + L::T_DN + b * DIM;
+          const TT *Z = rt + L::T_Z + b * DIM;
+          const TT Nb = (TT)shape_N<DIM>(q, b);
+          TT Bv[DIM];
+#pragma unroll
+          for (int k = 0; k < DIM; ++k) Bv[k] = B[k];
+          // K_uu (Eq. 11a): lam' a_i b_j + mu' a_j b_i + mu' (a.b) delta_ij
+#pragma unroll
+          for (int i = 0; i < DIM; ++i)
+#pragma unroll
+            for (int j = 0; j < DIM; ++j) {
+              if (i == j) {
+                TT s = acc[i][bb][i] + l2m[i] * Bv[i];
+#pragma unroll
+                for (int k = 0; k < DIM; ++k)
+                  if (k != i) s += ma[k] * Bv[k];
+                acc[i][bb][i] = s;
+              } else {
+                acc[i][bb][j] += la[i] * Bv[j] + ma[j] * Bv[i];
+              }
+            }
+          // K_ue (Eq. 11b) and K_eu (Eq. 11c)
+#pragma unroll
+          for (int i = 0; i < DIM; ++i) {
+            acc[i][bb][DIM] -= w[i] * Nb;
+            acc[DIM][bb][i] += nNa * Z[i];
+          }
+          // K_ee (Eq. 11d)
+          TT s = acc[DIM][bb][DIM] + ea * Nb;
+#pragma unroll
+          for (int k = 0; k < DIM; ++k) s += fa[k] * Bv[k];
+          acc[DIM][bb][DIM] = s;
+        }
+      }
+      TT *kout = Ke + ((int64_t)slot * NEN + a) * ND * (NEN * ND) + b0 * ND;
+#pragma unroll
+      for (int i = 0; i < ND; ++i)
+#pragma unroll
+        for (int bb = 0; bb < BC; ++bb)
+#pragma unroll
+          for (int j = 0; j < ND; ++j) kout[i * NEN * ND + bb * ND + j] = acc[i][bb][j];
+    }
+  }
+}
+
+template <int ELEM, typename TT, bool RES_ONLY>
+static cudaError_t launch_element_t(const MeshView &m, const MatConst &mc, const double *u,
+                                    const double *kh, const int32_t *list, int32_t n, TT *Ke, double *re,
+                                    cudaStream_t s) {
+  using L = ElemLayout<ELEM, TT>;
+  if (n <= 0) return cudaSuccess;
+  const size_t smem = L::bytes(RES_ONLY);
+  auto fn = element_kernel<ELEM, TT, RES_ONLY>;
+  cudaError_t err = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (err != cudaSuccess) return err;
+  const int grid = (n + L::EPB - 1) / L::EPB;
+  fn<<<grid, ELEM_THREADS, smem, s>>>(m, mc, u, kh, list, n, Ke, re);
+  return cudaGetLastError();
+}
+
+template <typename TT>
+cudaError_t launch_element(int elem, const MeshView &m, const MatConst &mc, const double *u,
+                           const double *kh, const int32_t *list, int32_t n, TT *Ke, double *re,
+                           bool res_only, cudaStream_t s) {
+#define LGDM_EL(E)                                                                          \
+  return res_only ? launch_element_t<E, TT, true>(m, mc, u, kh, list, n, Ke, re, s)         \
+                  : launch_element_t<E, TT, false>(m, mc, u, kh, list, n, Ke, re, s)
+  switch (elem) {
+    case LGDM_L2: LGDM_EL(LGDM_L2);
+    case LGDM_Q4: LGDM_EL(LGDM_Q4);
+    case LGDM_H8: LGDM_EL(LGDM_H8);
+  }
+#undef LGDM_EL
+  return cudaErrorInvalidValue;
+}
+template cudaError_t launch_element<double>(int, const MeshView &, const MatConst &, const double *,
+                                            const double *, const int32_t *, int32_t, double *,
+                                            double *, bool, cudaStream_t);
+template cudaError_t launch_element<float>(int, const MeshView &, const MatConst &, const double *,
+                                           const double *, const int32_t *, int32_t, float *, double *,
+                                           bool, cudaStream_t);
+
+// ------------------------------------------------------------------ gather
+template <int ND, int NEN, typename TT>
+__global__ void __launch_bounds__(256)
+gather_kernel(PatternView p, const TT *__restrict__ Ke, const double *__restrict__ re,
+              TT *__restrict__ vals, double *__restrict__ rraw, double *__restrict__ rhs) {
+  const int64_t pr = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (pr >= p.npairs) return;
+  const int32_t a = p.pair_node[pr], b = p.nbr[pr];
+  const int32_t pb = p.nbr_ptr[a];
+  const int32_t deg = p.nbr_ptr[a + 1] - pb;
+  const int32_t s = (int32_t)(pr - pb);
+  const bool diag = (a == b);
+  TT acc[ND][ND];
+#pragma unroll
+  for (int i = 0; i < ND; ++i)
+#pragma unroll
+    for (int j = 0; j < ND; ++j) acc[i][j] = (TT)0;
+  double racc[ND];
+#pragma unroll
+  for (int i = 0; i < ND; ++i) racc[i] = 0.0;
+  const int32_t c1 = p.pc_ptr[pr + 1];
+  for (int32_t c = p.pc_ptr[pr]; c < c1; ++c) {
+    const int32_t pk = p.pc[c];
+    const int64_t e = pk >> 6;
+    const int al = (pk >> 3) & 7, bl = pk & 7;
+    const TT *blk = Ke + ((e * NEN + al) * ND) * (NEN * ND) + bl * ND;
+#pragma unroll
+    for (int i = 0; i < ND; ++i)
+#pragma unroll
+      for (int j = 0; j < ND; ++j) acc[i][j] += blk[i * NEN * ND + j];
+    if (diag) {
+      const double *rb = re + (e * NEN + al) * ND;
+#pragma unroll
+      for (int i = 0; i < ND; ++i) racc[i] += rb[i];
+    }
+  }
+  const int64_t vbase = (int64_t)ND * ND * pb + (int64_t)ND * s;
+#pragma unroll
+  for (int i = 0; i < ND; ++i) {
+    const int64_t row = (int64_t)ND * a + i;
+    const bool rdir = p.isdir[row];
+#pragma unroll
+    for (int j = 0; j < ND; ++j) {
+      const int64_t col = (int64_t)ND * b + j;
+      TT v = acc[i][j];
+      if (rdir || p.isdir[col]) v = (row == col) ? (TT)1 : (TT)0;
+      vals[vbase + (int64_t)i * ND * deg + j] = v;
+    }
+    if (diag) {
+      rraw[row] = racc[i];
+      rhs[row] = rdir ? 0.0 : -racc[i];
+    }
+  }
+}
+
+template <typename TT>
+cudaError_t launch_gather(int elem, const PatternView &p, const TT *Ke, const double *re, TT *vals,
+                          double *rraw, double *rhs, cudaStream_t s) {
+  const int grid = (int)((p.npairs + 255) / 256);
+  switch (elem) {
+    case LGDM_L2: gather_kernel<2, 2, TT><<<grid, 256, 0, s>>>(p, Ke, re, vals, rraw, rhs); break;
+    case LGDM_Q4: gather_kernel<3, 4, TT><<<grid, 256, 0, s>>>(p, Ke, re, vals, rraw, rhs); break;
+    case LGDM_H8: gather_kernel<4, 8, TT><<<grid, 256, 0, s>>>(p, Ke, re, vals, rraw, rhs); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+template cudaError_t launch_gather<double>(int, const PatternView &, const double *, const double *,
+                                           double *, double *, double *, cudaStream_t);
+template cudaError_t launch_gather<float>(int, const PatternView &, const float *, const double *,
+                                          float *, double *, double *, cudaStream_t);
+
+// ------------------------------------------------------------------ preconditioner
+// Inverse of each node's nd x nd diagonal block (Gauss-Jordan, partial
+// pivoting, in double), or of its diagonal only (point Jacobi).
+template <int ND, typename TT>
+__global__ void precond_kernel(PatternView p, const TT *__restrict__ vals, int kind, TT *__restrict__ minv) {
+  const int32_t a = blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= p.nnode) return;
+  const int32_t pb = p.nbr_ptr[a], deg = p.nbr_ptr[a + 1] - pb;
+  const int32_t s = p.diag_pair[a] - pb;
+  const int64_t vbase = (int64_t)ND * ND * pb + (int64_t)ND * s;
+  double M[ND][2 * ND];
+#pragma unroll
+  for (int i = 0; i < ND; ++i)
+#pragma unroll
+    for (int j = 0; j < ND; ++j) {
+      const double v = (double)vals[vbase + (int64_t)i * ND * deg + j];
+      M[i][j] = (kind == LGDM_PRECOND_NODE_BLOCK || i == j) ? v : 0.0;
+      M[i][ND + j] = (i == j) ? 1.0 : 0.0;
+    }
+#pragma unroll
+  for (int c = 0; c < ND; ++c) {
+    int piv = c;
+    double best = fabs(M[c][c]);
+#pragma unroll
+    for (int r = c + 1; r < ND; ++r)
+      if (fabs(M[r][c]) > best) { best = fabs(M[r][c]); piv = r; }
+#pragma unroll
+    for (int r = 0; r < ND; ++r)
+      if (r == piv && piv != c) {
+#pragma unroll
+        for (int k = 0; k < 2 * ND; ++k) { const double t = M[c][k]; M[c][k] = M[r][k]; M[r][k] = t; }
+      }
+    const double inv = (M[c][c] != 0.0) ? 1.0 / M[c][c] : 0.0;
+#pragma unroll
+    for (int k = 0; k < 2 * ND; ++k) M[c][k] *= inv;
+#pragma unroll
+    for (int r = 0; r < ND; ++r)
+      if (r != c) {
+        const double f = M[r][c];
+#pragma unroll
+        for (int k = 0; k < 2 * ND; ++k) M[r][k] -= f * M[c][k];
+      }
+  }
+#pragma unroll
+  for (int i = 0; i < ND; ++i)
+#pragma unroll
+    for (int j = 0; j < ND; ++j) minv[((int64_t)a * ND + i) * ND + j] = (TT)M[i][ND + j];
+}
+
+template <typename TT>
+cudaError_t launch_precond(int nd, const PatternView &p, const TT *vals, int kind, TT *minv, cudaStream_t s) {
+  const int grid = (p.nnode + 127) / 128;
+  switch (nd) {
+    case 2: precond_kernel<2, TT><<<grid, 128, 0, s>>>(p, vals, kind, minv); break;
+    case 3: precond_kernel<3, TT><<<grid, 128, 0, s>>>(p, vals, kind, minv); break;
+    case 4: precond_kernel<4, TT><<<grid, 128, 0, s>>>(p, vals, kind, minv); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+template cudaError_t launch_precond<double>(int, const PatternView &, const double *, int, double *, cudaStream_t);
+template cudaError_t launch_precond<float>(int, const PatternView &, const float *, int, float *, cudaStream_t);
+
+// ------------------------------------------------------------------ small kernels
+__global__ void set_dirichlet_kernel(double *u, const int32_t *dof, const double *scale, int32_t n, double load) {
+  const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) u[dof[i]] = scale[i] * load;
+}
+cudaError_t launch_set_dirichlet(double *u, const int32_t *dof, const double *scale, int32_t n, double load,
+                                 cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  set_dirichlet_kernel<<<(n + 255) / 256, 256, 0, s>>>(u, dof, scale, n, load);
+  return cudaGetLastError();
+}
+
+// History commit (Eq. A.2): kappa_hist <- max(kappa_hist, ebar at the Gauss point).
+template <int ELEM>
+__global__ void commit_kernel(MeshView m, const double *__restrict__ u, double *__restrict__ kh) {
+  constexpr int DIM = Elem<ELEM>::DIM, NEN = Elem<ELEM>::NEN, ND = DIM + 1;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)m.nel * NEN) return;
+  const int64_t e = t / NEN;
+  const int q = (int)(t % NEN);
+  double eb = 0.0;
+#pragma unroll
+  for (int b = 0; b < NEN; ++b) eb += shape_N<DIM>(q, b) * u[(int64_t)m.conn[e * NEN + b] * ND + DIM];
+  kh[t] = fmax(kh[t], eb);
+}
+cudaError_t launch_commit(int elem, const MeshView &m, const double *u, double *kh, cudaStream_t s) {
+  const int nen = (elem == LGDM_L2) ? 2 : (elem == LGDM_Q4) ? 4 : 8;
+  const int64_t n = (int64_t)m.nel * nen;
+  const int grid = (int)((n + 255) / 256);
+  switch (elem) {
+    case LGDM_L2: commit_kernel<LGDM_L2><<<grid, 256, 0, s>>>(m, u, kh); break;
+    case LGDM_Q4: commit_kernel<LGDM_Q4><<<grid, 256, 0, s>>>(m, u, kh); break;
+    case LGDM_H8: commit_kernel<LGDM_H8><<<grid, 256, 0, s>>>(m, u, kh); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+__global__ void damage_field_kernel(MatConst mc, const double *kh, int64_t n, double *out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double k = kh[i];
+  double D = 0.0;
+  if (k > mc.kappa0) D = 1.0 - mc.kappa0 / k * (1.0 - mc.alpha + mc.alpha * exp(-mc.beta * (k - mc.kappa0)));
+  out[i] = D;
+}
+cudaError_t launch_damage_field(const MatConst &mc, const double *kh, int64_t n, double *out, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  damage_field_kernel<<<(int)((n + 255) / 256), 256, 0, s>>>(mc, kh, n, out);
+  return cudaGetLastError();
+}
+
+// Reaction: sum_k w[k] re[idx[k]], one block, fixed summation order.
+__global__ void reaction_sum_kernel(const double *re, const int32_t *idx, const double *w, int32_t n, double *out) {
+  __shared__ double sh[256];
+  double s = 0.0;
+  for (int32_t k = threadIdx.x; k < n; k += 256) s += w[k] * re[idx[k]];
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int off = 128; off > 0; off >>= 1) {
+    if ((int)threadIdx.x < off) sh[threadIdx.x] += sh[threadIdx.x + off];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = sh[0];
+}
+cudaError_t launch_reaction_sum(const double *re, const int32_t *idx, const double *w, int32_t n, double *out,
+                                cudaStream_t s) {
+  reaction_sum_kernel<<<1, 256, 0, s>>>(re, idx, w, n, out);
+  return cudaGetLastError();
+}
+
+}  // namespace lgdm

@@ -1,0 +1,126 @@
+// Internal declarations of the LGDM CUDA library (not part of the C ABI).
+#pragma once
+#include <cstdint>
+#include <cstddef>
+#include <cuda_runtime.h>
+#include "lgdm.h"
+
+namespace lgdm {
+
+// ---------------------------------------------------------------- element traits
+template <int ELEM> struct Elem;
+template <> struct Elem<LGDM_L2> { static constexpr int DIM = 1, NEN = 2, NV = 1; };
+template <> struct Elem<LGDM_Q4> { static constexpr int DIM = 2, NEN = 4, NV = 3; };
+template <> struct Elem<LGDM_H8> { static constexpr int DIM = 3, NEN = 8, NV = 6; };
+
+// Reference node signs; the first 2 rows serve the bar, the first 4 the quad.
+__host__ __device__ constexpr int ref_sign(int a, int i) {
+  return ((i == 0) ? ((a & 3) == 1 || (a & 3) == 2) : (i == 1) ? ((a & 3) >= 2) : (a >= 4)) ? 1 : -1;
+}
+// 2-point Gauss rule: factor (1 + xi_q xi_a)/2 with xi_q = +-1/sqrt(3).
+constexpr double INV_SQRT3 = 0.57735026918962576451;
+constexpr double GP_P = 0.5 + 0.5 * INV_SQRT3;   // signs agree
+constexpr double GP_M = 0.5 - 0.5 * INV_SQRT3;   // signs differ
+
+template <int DIM>
+__host__ __device__ constexpr double shape_N(int q, int a) {
+  double v = 1.0;
+  for (int i = 0; i < DIM; ++i) v *= (ref_sign(q, i) == ref_sign(a, i)) ? GP_P : GP_M;
+  return v;
+}
+// dN_a / dxi_j at Gauss point q.
+template <int DIM>
+__host__ __device__ constexpr double shape_dN(int q, int a, int j) {
+  double v = 0.5 * ref_sign(a, j);
+  for (int i = 0; i < DIM; ++i)
+    if (i != j) v *= (ref_sign(q, i) == ref_sign(a, i)) ? GP_P : GP_M;
+  return v;
+}
+
+// ---------------------------------------------------------------- material
+struct MatConst {
+  double lam, mu;             // Lame constants (2D plane strain / 3D); 1D: lam = E, mu = 0
+  double evm_a, evm_b2, evm_cJ, inv2k;   // Eq. A.3 coefficients
+  double kappa0, alpha, beta;            // Eq. A.1
+  double g_a, g_b, eta;                  // g = g_a e^{-eta D} + g_b  (Eq. A.4)
+  double h, c;
+};
+
+MatConst make_matconst(const lgdm_material &m, int dim);
+
+// ---------------------------------------------------------------- device views
+struct MeshView {
+  const double *x, *y, *z;
+  const int32_t *conn;        // [nel*nen]
+  const double *e_scale, *vol_scale;
+  int32_t nel, nnode;
+};
+
+struct PatternView {
+  int32_t nnode;
+  int64_t npairs;
+  const int32_t *nbr_ptr;     // [nnode+1]
+  const int32_t *nbr;         // [npairs] neighbour node of each pair (sorted per node)
+  const int32_t *pair_node;   // [npairs] owning node of each pair
+  const int32_t *pc_ptr;      // [npairs+1] contributions of each pair
+  const int32_t *pc;          // [ncontrib] packed (element*64 + a_loc*8 + b_loc)
+  const int32_t *diag_pair;   // [nnode] pair index of (a, a)
+  const uint8_t *isdir;       // [ndof]
+};
+
+// Result block written by the persistent Krylov kernel.
+struct SolveResult {
+  int32_t iters;
+  int32_t status;             // 0 ok, 1 max iterations, 2 breakdown, 3 nonfinite, 4 barrier timeout (max wins)
+  int32_t converged;          // Newton test after the fused update
+  int32_t pad;
+  double rel_res;
+  double bnorm;
+  double norms[4];            // ||du||, ||u||, ||de||, ||e||
+};
+
+// ---------------------------------------------------------------- launchers
+template <typename TT>
+cudaError_t launch_element(int elem, const MeshView &m, const MatConst &mc, const double *u,
+                           const double *kappa_hist, const int32_t *elem_list, int32_t n_elem,
+                           TT *Ke, double *re, bool residual_only, cudaStream_t s);
+template <typename TT>
+cudaError_t launch_gather(int elem, const PatternView &p, const TT *Ke, const double *re,
+                          TT *vals, double *rraw, double *rhs, cudaStream_t s);
+template <typename TT>
+cudaError_t launch_precond(int nd, const PatternView &p, const TT *vals, int kind, TT *minv,
+                           cudaStream_t s);
+cudaError_t launch_set_dirichlet(double *u, const int32_t *dof, const double *scale, int32_t n,
+                                 double load, cudaStream_t s);
+cudaError_t launch_commit(int elem, const MeshView &m, const double *u, double *kappa_hist,
+                          cudaStream_t s);
+cudaError_t launch_damage_field(const MatConst &mc, const double *kappa_hist, int64_t n, double *out,
+                                cudaStream_t s);
+cudaError_t launch_reaction_sum(const double *re, const int32_t *idx, const double *w, int32_t n,
+                                double *out, cudaStream_t s);
+
+constexpr int KRYLOV_THREADS = 256;
+
+struct KrylovArgs {
+  int32_t nd, nnode;
+  int32_t max_iter;
+  int32_t pad;
+  double rtol, newton_tol;
+  PatternView p;
+  const void *vals;           // TT [nnz]
+  const void *minv;           // TT [nnode*nd*nd]
+  const double *rhs;          // [ndof]
+  double *x, *r, *r0, *pv, *v, *sv, *t, *ph, *sh;   // [ndof] each
+  double *u;                  // [ndof] state (modes 1 and 2)
+  double *partial;            // [3 slots][4 values][gridDim]
+  unsigned int *bar_count, *bar_gen;
+  SolveResult *res;
+};
+// mode 0: solve; 1: solve, u += delta, Newton test; 2: update and test only.
+// phT / shT: TT copies of the preconditioned vectors (may alias ph / sh for double).
+template <typename TT>
+cudaError_t launch_bicgstab(const KrylovArgs &a, void *phT, void *shT, int nblocks, int mode, cudaStream_t s);
+template <typename TT>
+int bicgstab_max_blocks();
+
+}  // namespace lgdm
