@@ -148,6 +148,10 @@ lgdm_status lgdm_get_sizes(const lgdm_sim *sim, lgdm_sizes *out);
  * (either may be NULL to keep it).  The result is also the committed state. */
 lgdm_status lgdm_set_state(lgdm_sim *sim, const double *u, const double *kappa_hist);
 
+/* Return to the initial state on the device (u = 0, kappa_hist = kappa0,
+ * committed load 0) without re-creating the simulation.  Asynchronous. */
+lgdm_status lgdm_reset_state(lgdm_sim *sim);
+
 /* Copy a field (lgdm_field) into host memory of n doubles (n must match). */
 lgdm_status lgdm_get_field(lgdm_sim *sim, int32_t which, double *host_dst, size_t n);
 
@@ -195,6 +199,22 @@ lgdm_status lgdm_commit(lgdm_sim *sim);
  * 2 breakdown, 3 non-finite, 4 barrier timeout), relative residual, and the
  * norms ||du||, ||u||, ||de||, ||e|| of the last update (norms4 may be NULL). */
 lgdm_status lgdm_last_solve(lgdm_sim *sim, int32_t *iters, int32_t *status, double *rel_res, double *norms4);
+
+/* Phase timers (CUDA events recorded on the simulation's stream around each
+ * launch).  Phases: 0 element integration, 1 CSR gather + Dirichlet rows,
+ * 2 preconditioner set-up, 3 Krylov solve + update, 4 commit + reaction,
+ * 5 begin_step.  lgdm_get_timers synchronises the stream and returns, per
+ * phase, the summed milliseconds and the number of launches timed since the
+ * last reset (arrays of LGDM_NPHASES entries; either may be NULL). */
+#define LGDM_NPHASES 6
+lgdm_status lgdm_enable_timers(lgdm_sim *sim, int32_t on);
+lgdm_status lgdm_get_timers(lgdm_sim *sim, double *ms, int64_t *launches);
+lgdm_status lgdm_reset_timers(lgdm_sim *sim);
+
+/* Counters since creation: [0] kernel launches, [1] assemblies,
+ * [2] Krylov iterations, [3] Newton iterations, [4] committed load steps,
+ * [5] increment halvings.  n entries are written (n <= 6). */
+lgdm_status lgdm_get_counters(const lgdm_sim *sim, int64_t *counters, int32_t n);
 
 /* Reaction at the last committed state.  Synchronises. */
 lgdm_status lgdm_get_reaction(lgdm_sim *sim, double *reaction);

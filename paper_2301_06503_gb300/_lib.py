@@ -13,6 +13,9 @@ L2, Q4, H8 = 1, 2, 3
 PREC_FP64, PREC_FP32_TANGENT = 0, 1
 PRECOND_JACOBI, PRECOND_NODE_BLOCK = 0, 1
 FIELD_U, FIELD_KAPPA_HIST, FIELD_DAMAGE, FIELD_DELTA, FIELD_RESIDUAL, FIELD_RHS = range(6)
+NPHASES = 6
+PHASES = ("element", "gather", "precond", "krylov", "commit", "begin_step")
+COUNTERS = ("kernel_launches", "assemblies", "krylov_iters", "newton_iters", "load_steps", "halvings")
 STATUS = {0: "ok", 1: "invalid argument", 2: "workspace too small", 3: "CUDA error",
           4: "Newton did not converge", 5: "non-finite value", 6: "device wait timed out",
           7: "call out of order"}
@@ -65,6 +68,7 @@ _SIGS = {
     "lgdm_last_error": (C.c_char_p, [C.c_void_p]),
     "lgdm_get_sizes": (C.c_int, [C.c_void_p, C.POINTER(Sizes)]),
     "lgdm_set_state": (C.c_int, [C.c_void_p, _dp, _dp]),
+    "lgdm_reset_state": (C.c_int, [C.c_void_p]),
     "lgdm_get_field": (C.c_int, [C.c_void_p, C.c_int32, _dp, C.c_size_t]),
     "lgdm_begin_step": (C.c_int, [C.c_void_p, C.c_double]),
     "lgdm_assemble": (C.c_int, [C.c_void_p]),
@@ -76,6 +80,10 @@ _SIGS = {
     "lgdm_commit": (C.c_int, [C.c_void_p]),
     "lgdm_last_solve": (C.c_int, [C.c_void_p, _ip, _ip, _dp, _dp]),
     "lgdm_get_reaction": (C.c_int, [C.c_void_p, _dp]),
+    "lgdm_enable_timers": (C.c_int, [C.c_void_p, C.c_int32]),
+    "lgdm_get_timers": (C.c_int, [C.c_void_p, _dp, C.POINTER(C.c_int64)]),
+    "lgdm_reset_timers": (C.c_int, [C.c_void_p]),
+    "lgdm_get_counters": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.c_int32]),
 }
 
 _lib = None

@@ -119,6 +119,11 @@ struct Carver {
 
 }  // namespace
 
+struct lgdm_sim;
+namespace {
+void resolve_timers(lgdm_sim *s);
+}
+
 struct lgdm_sim {
   int elem = 0, dim = 0, nen = 0, ngp = 0, nd = 0;
   int32_t nnode = 0, nel = 0;
@@ -145,18 +150,32 @@ struct lgdm_sim {
   double *u = nullptr, *u_commit = nullptr, *kappa_hist = nullptr;
   void *Ke = nullptr, *vals = nullptr, *minv = nullptr;
   double *re = nullptr, *rraw = nullptr, *rhs = nullptr;
-  double *kv[9] = {};
-  void *phT = nullptr, *shT = nullptr;
+  double *kv[10] = {};
   double *partial = nullptr, *field_tmp = nullptr, *reaction = nullptr;
   unsigned int *bar = nullptr;
   SolveResult *res = nullptr;
   int krylov_blocks = 1;
   SolveResult last{};
+  // phase timers and counters
+  bool timers_on = false;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_pending;
+  double phase_ms[LGDM_NPHASES] = {};
+  int64_t phase_n[LGDM_NPHASES] = {};
+  int64_t counters[6] = {};
   // host copies
   std::vector<int32_t> h_nbr_ptr, h_nbr;
   std::string err;
   double load_commit = 0.0;
   bool assembled = false;
+
+  ~lgdm_sim() {
+    for (auto &p : ev_pending) {
+      cudaEventDestroy(p.second.first);
+      cudaEventDestroy(p.second.second);
+    }
+    for (auto e : ev_pool) cudaEventDestroy(e);
+  }
 
   MeshView mesh_view() const {
     return MeshView{x, y, z, conn, e_scale, vol_scale, nel, nnode};
@@ -172,6 +191,50 @@ lgdm_status fail(lgdm_sim *s, lgdm_status st, const std::string &msg) {
   if (s) s->err = msg;
   else g_last_error = msg;
   return st;
+}
+
+cudaEvent_t take_event(lgdm_sim *s) {
+  if (!s->ev_pool.empty()) {
+    cudaEvent_t e = s->ev_pool.back();
+    s->ev_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  return e;
+}
+
+// Times one phase with an event pair when timers are on.
+struct PhaseTimer {
+  lgdm_sim *s;
+  int phase;
+  cudaEvent_t a = nullptr;
+  PhaseTimer(lgdm_sim *s_, int ph) : s(s_), phase(ph) {
+    if (s->timers_on && (a = take_event(s))) cudaEventRecord(a, s->stream);
+  }
+  ~PhaseTimer() {
+    if (!a) return;
+    cudaEvent_t b = take_event(s);
+    if (!b) {
+      s->ev_pool.push_back(a);
+      return;
+    }
+    cudaEventRecord(b, s->stream);
+    s->ev_pending.push_back({phase, {a, b}});
+  }
+};
+
+void resolve_timers(lgdm_sim *s) {
+  for (auto &p : s->ev_pending) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, p.second.first, p.second.second) == cudaSuccess) {
+      s->phase_ms[p.first] += ms;
+      s->phase_n[p.first] += 1;
+    }
+    s->ev_pool.push_back(p.second.first);
+    s->ev_pool.push_back(p.second.second);
+  }
+  s->ev_pending.clear();
 }
 
 #define LGDM_CUDA(sim, call)                                                                  \
@@ -223,9 +286,7 @@ void carve(lgdm_sim &s, Carver &c) {
   s.minv = c.take<char>((size_t)s.nnode * s.nd * s.nd * s.tsize);
   s.rraw = c.take<double>(s.ndof);
   s.rhs = c.take<double>(s.ndof);
-  for (int k = 0; k < 9; ++k) s.kv[k] = c.take<double>(s.ndof);
-  s.phT = c.take<char>((size_t)s.ndof * s.tsize);
-  s.shT = c.take<char>((size_t)s.ndof * s.tsize);
+  for (int k = 0; k < 10; ++k) s.kv[k] = c.take<double>(s.ndof);
   s.partial = c.take<double>((size_t)3 * 4 * std::max(s.krylov_blocks, 1));
   s.field_tmp = c.take<double>(std::max((size_t)s.nel * s.ngp, (size_t)s.ndof));
   s.reaction = c.take<double>(1);
@@ -485,6 +546,18 @@ lgdm_status lgdm_set_state(lgdm_sim *s, const double *u, const double *kh) {
   return LGDM_OK;
 }
 
+lgdm_status lgdm_reset_state(lgdm_sim *s) {
+  if (!s) return fail(nullptr, LGDM_ERR_INVALID_ARG, "NULL handle");
+  LGDM_CUDA(s, cudaMemsetAsync(s->u, 0, sizeof(double) * s->ndof, s->stream));
+  LGDM_CUDA(s, cudaMemsetAsync(s->u_commit, 0, sizeof(double) * s->ndof, s->stream));
+  LGDM_CUDA(s, launch_fill(s->kappa_hist, (int64_t)s->nel * s->ngp, s->mat.kappa0, s->stream));
+  LGDM_CUDA(s, cudaMemsetAsync(s->reaction, 0, sizeof(double), s->stream));
+  s->counters[0] += 1;
+  s->load_commit = 0.0;
+  s->assembled = false;
+  return LGDM_OK;
+}
+
 lgdm_status lgdm_get_field(lgdm_sim *s, int32_t which, double *dst, size_t n) {
   if (!s || !dst) return fail(s, LGDM_ERR_INVALID_ARG, "NULL argument");
   const size_t ngpt = (size_t)s->nel * s->ngp;
@@ -511,8 +584,10 @@ lgdm_status lgdm_get_field(lgdm_sim *s, int32_t which, double *dst, size_t n) {
 
 lgdm_status lgdm_begin_step(lgdm_sim *s, double load) {
   if (!s) return fail(nullptr, LGDM_ERR_INVALID_ARG, "NULL handle");
+  PhaseTimer pt(s, 5);
   LGDM_CUDA(s, cudaMemcpyAsync(s->u, s->u_commit, sizeof(double) * s->ndof, cudaMemcpyDeviceToDevice, s->stream));
   LGDM_CUDA(s, launch_set_dirichlet(s->u, s->dir_dof, s->dir_scale, s->ndir, load, s->stream));
+  s->counters[0] += 1;
   s->assembled = false;
   return LGDM_OK;
 }
@@ -522,20 +597,40 @@ lgdm_status lgdm_assemble(lgdm_sim *s) {
   const MeshView mv = s->mesh_view();
   const PatternView pv = s->pattern_view();
   if (s->opt.precision == LGDM_PREC_FP32_TANGENT) {
-    LGDM_CUDA(s, launch_element<float>(s->elem, mv, s->mc, s->u, s->kappa_hist, nullptr, s->nel,
-                                       static_cast<float *>(s->Ke), s->re, false, s->stream));
-    LGDM_CUDA(s, launch_gather<float>(s->elem, pv, static_cast<float *>(s->Ke), s->re,
-                                      static_cast<float *>(s->vals), s->rraw, s->rhs, s->stream));
-    LGDM_CUDA(s, launch_precond<float>(s->nd, pv, static_cast<float *>(s->vals), s->opt.precond,
-                                       static_cast<float *>(s->minv), s->stream));
+    {
+      PhaseTimer pt(s, 0);
+      LGDM_CUDA(s, launch_element<float>(s->elem, mv, s->mc, s->u, s->kappa_hist, nullptr, s->nel,
+                                         static_cast<float *>(s->Ke), s->re, false, s->stream));
+    }
+    {
+      PhaseTimer pt(s, 1);
+      LGDM_CUDA(s, launch_gather<float>(s->elem, pv, static_cast<float *>(s->Ke), s->re,
+                                        static_cast<float *>(s->vals), s->rraw, s->rhs, s->stream));
+    }
+    {
+      PhaseTimer pt(s, 2);
+      LGDM_CUDA(s, launch_precond<float>(s->nd, pv, static_cast<float *>(s->vals), s->opt.precond,
+                                         static_cast<float *>(s->minv), s->stream));
+    }
   } else {
-    LGDM_CUDA(s, launch_element<double>(s->elem, mv, s->mc, s->u, s->kappa_hist, nullptr, s->nel,
-                                        static_cast<double *>(s->Ke), s->re, false, s->stream));
-    LGDM_CUDA(s, launch_gather<double>(s->elem, pv, static_cast<double *>(s->Ke), s->re,
-                                       static_cast<double *>(s->vals), s->rraw, s->rhs, s->stream));
-    LGDM_CUDA(s, launch_precond<double>(s->nd, pv, static_cast<double *>(s->vals), s->opt.precond,
-                                        static_cast<double *>(s->minv), s->stream));
+    {
+      PhaseTimer pt(s, 0);
+      LGDM_CUDA(s, launch_element<double>(s->elem, mv, s->mc, s->u, s->kappa_hist, nullptr, s->nel,
+                                          static_cast<double *>(s->Ke), s->re, false, s->stream));
+    }
+    {
+      PhaseTimer pt(s, 1);
+      LGDM_CUDA(s, launch_gather<double>(s->elem, pv, static_cast<double *>(s->Ke), s->re,
+                                         static_cast<double *>(s->vals), s->rraw, s->rhs, s->stream));
+    }
+    {
+      PhaseTimer pt(s, 2);
+      LGDM_CUDA(s, launch_precond<double>(s->nd, pv, static_cast<double *>(s->vals), s->opt.precond,
+                                          static_cast<double *>(s->minv), s->stream));
+    }
   }
+  s->counters[0] += 3;
+  s->counters[1] += 1;
   s->assembled = true;
   return LGDM_OK;
 }
@@ -600,6 +695,8 @@ KrylovArgs krylov_args(lgdm_sim *s) {
   a.t = s->kv[6];
   a.ph = s->kv[7];
   a.sh = s->kv[8];
+  a.xb = s->kv[9];
+  a.stall_iters = std::max(500, s->opt.max_krylov / 4);
   a.u = s->u;
   a.partial = s->partial;
   a.bar_count = s->bar;
@@ -610,12 +707,18 @@ KrylovArgs krylov_args(lgdm_sim *s) {
 
 lgdm_status run_krylov(lgdm_sim *s, int mode, SolveResult *out) {
   const KrylovArgs a = krylov_args(s);
-  if (s->opt.precision == LGDM_PREC_FP32_TANGENT)
-    LGDM_CUDA(s, launch_bicgstab<float>(a, s->phT, s->shT, s->krylov_blocks, mode, s->stream));
-  else
-    LGDM_CUDA(s, launch_bicgstab<double>(a, s->kv[7], s->kv[8], s->krylov_blocks, mode, s->stream));
+  {
+    PhaseTimer pt(s, 3);
+    if (s->opt.precision == LGDM_PREC_FP32_TANGENT)
+      LGDM_CUDA(s, launch_bicgstab<float>(a, s->krylov_blocks, mode, s->stream));
+    else
+      LGDM_CUDA(s, launch_bicgstab<double>(a, s->krylov_blocks, mode, s->stream));
+  }
+  s->counters[0] += 1;
   LGDM_CUDA(s, cudaMemcpyAsync(out, s->res, sizeof(SolveResult), cudaMemcpyDeviceToHost, s->stream));
   LGDM_CUDA(s, cudaStreamSynchronize(s->stream));
+  if (mode != 2) s->counters[2] += out->iters;
+  if (s->timers_on) resolve_timers(s);
   if (mode == 2) {
     s->last.converged = out->converged;
     for (int k = 0; k < 4; ++k) s->last.norms[k] = out->norms[k];
@@ -663,6 +766,9 @@ lgdm_status lgdm_newton_step(lgdm_sim *s, int32_t *converged, int32_t *krylov_it
 
 lgdm_status lgdm_commit(lgdm_sim *s) {
   if (!s) return fail(nullptr, LGDM_ERR_INVALID_ARG, "NULL handle");
+  PhaseTimer pt(s, 4);
+  s->counters[0] += (s->n_reac > 0) ? 3 : 1;
+  s->counters[4] += 1;
   LGDM_CUDA(s, launch_commit(s->elem, s->mesh_view(), s->u, s->kappa_hist, s->stream));
   LGDM_CUDA(s, cudaMemcpyAsync(s->u_commit, s->u, sizeof(double) * s->ndof, cudaMemcpyDeviceToDevice, s->stream));
   if (s->n_reac > 0) {
@@ -690,6 +796,40 @@ lgdm_status lgdm_last_solve(lgdm_sim *s, int32_t *iters, int32_t *status, double
   return LGDM_OK;
 }
 
+lgdm_status lgdm_enable_timers(lgdm_sim *s, int32_t on) {
+  if (!s) return fail(nullptr, LGDM_ERR_INVALID_ARG, "NULL handle");
+  s->timers_on = on != 0;
+  return LGDM_OK;
+}
+
+lgdm_status lgdm_get_timers(lgdm_sim *s, double *ms, int64_t *launches) {
+  if (!s) return fail(nullptr, LGDM_ERR_INVALID_ARG, "NULL handle");
+  LGDM_CUDA(s, cudaStreamSynchronize(s->stream));
+  resolve_timers(s);
+  for (int k = 0; k < LGDM_NPHASES; ++k) {
+    if (ms) ms[k] = s->phase_ms[k];
+    if (launches) launches[k] = s->phase_n[k];
+  }
+  return LGDM_OK;
+}
+
+lgdm_status lgdm_reset_timers(lgdm_sim *s) {
+  if (!s) return fail(nullptr, LGDM_ERR_INVALID_ARG, "NULL handle");
+  LGDM_CUDA(s, cudaStreamSynchronize(s->stream));
+  resolve_timers(s);
+  for (int k = 0; k < LGDM_NPHASES; ++k) {
+    s->phase_ms[k] = 0.0;
+    s->phase_n[k] = 0;
+  }
+  return LGDM_OK;
+}
+
+lgdm_status lgdm_get_counters(const lgdm_sim *s, int64_t *c, int32_t n) {
+  if (!s || !c || n < 0 || n > 6) return fail(nullptr, LGDM_ERR_INVALID_ARG, "bad counters request");
+  for (int k = 0; k < n; ++k) c[k] = s->counters[k];
+  return LGDM_OK;
+}
+
 lgdm_status lgdm_get_reaction(lgdm_sim *s, double *reaction) {
   if (!s || !reaction) return fail(s, LGDM_ERR_INVALID_ARG, "NULL argument");
   LGDM_CUDA(s, cudaMemcpyAsync(reaction, s->reaction, sizeof(double), cudaMemcpyDeviceToHost, s->stream));
@@ -710,6 +850,7 @@ lgdm_status attempt(lgdm_sim *s, double load, bool *done, int32_t *iters) {
     int32_t conv = 0;
     st = lgdm_newton_step(s, &conv, nullptr);
     ++*iters;
+    s->counters[3] += 1;
     if (st == LGDM_ERR_NONFINITE) return LGDM_OK;   // treated like divergence: halve
     if (st != LGDM_OK) return st;
     if (conv) {
@@ -736,6 +877,7 @@ lgdm_status advance(lgdm_sim *s, double from, double to, int depth, int32_t *ite
                     " halvings");
   }
   const double mid = 0.5 * (from + to);
+  s->counters[5] += 1;
   st = advance(s, from, mid, depth + 1, iters);
   if (st != LGDM_OK) return st;
   return advance(s, mid, to, depth + 1, iters);

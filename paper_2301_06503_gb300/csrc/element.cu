@@ -639,6 +639,16 @@ cudaError_t launch_commit(int elem, const MeshView &m, const double *u, double *
   return cudaGetLastError();
 }
 
+__global__ void fill_kernel(double *p, int64_t n, double v) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) p[i] = v;
+}
+cudaError_t launch_fill(double *p, int64_t n, double v, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  fill_kernel<<<(int)((n + 255) / 256), 256, 0, s>>>(p, n, v);
+  return cudaGetLastError();
+}
+
 __global__ void damage_field_kernel(MatConst mc, const double *kh, int64_t n, double *out) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;

@@ -83,25 +83,28 @@ __device__ double grid_sum(const double *part, int nb) {
   return block_sum(v);
 }
 
-// One row of y = K x.  x is written by other blocks during the launch, so it
-// is read through L2 (__ldcg), never through a stale L1 line.
+// One row of y = K x.  The matrix may be float (FP32 tangent), but x is
+// read and the products are accumulated in double: the smooth, low-energy
+// vectors BiCGSTAB must resolve have |Kx| far below |K||x|, and a float
+// accumulation would lose them.  x is written by other blocks during the
+// launch, so it is read through L2 (__ldcg), never through a stale L1 line.
 template <int ND, typename TT>
-__device__ __forceinline__ double spmv_row(const PatternView &p, const TT *__restrict__ vals, const TT *x,
+__device__ __forceinline__ double spmv_row(const PatternView &p, const TT *__restrict__ vals, const double *x,
                                            int64_t row) {
   const int32_t a = (int32_t)(row / ND), i = (int32_t)(row % ND);
   const int32_t pb = p.nbr_ptr[a], deg = p.nbr_ptr[a + 1] - pb;
   const TT *v = vals + (int64_t)ND * ND * pb + (int64_t)i * ND * deg;
-  TT acc = (TT)0;
+  double acc = 0.0;
   for (int32_t s = 0; s < deg; ++s) {
-    const TT *xb = x + (int64_t)ND * p.nbr[pb + s];
+    const double *xb = x + (int64_t)ND * p.nbr[pb + s];
 #pragma unroll
-    for (int j = 0; j < ND; ++j) acc += v[ND * s + j] * __ldcg(xb + j);
+    for (int j = 0; j < ND; ++j) acc += (double)v[ND * s + j] * __ldcg(xb + j);
   }
-  return (double)acc;
+  return acc;
 }
 
 template <int ND, typename TT>
-__device__ __forceinline__ void precond_rows(const TT *__restrict__ minv, const double *in, double *out, TT *outT,
+__device__ __forceinline__ void precond_rows(const TT *__restrict__ minv, const double *in, double *out,
                                              int64_t r0, int64_t r1) {
   for (int64_t row = r0 + threadIdx.x; row < r1; row += KT) {
     const int64_t a = row / ND;
@@ -112,12 +115,11 @@ __device__ __forceinline__ void precond_rows(const TT *__restrict__ minv, const 
 #pragma unroll
     for (int j = 0; j < ND; ++j) s += m[j] * (TT)x[j];
     out[row] = (double)s;
-    outT[row] = s;
   }
 }
 
 template <int ND, typename TT>
-__global__ void __launch_bounds__(KT) bicgstab_kernel(KrylovArgs A, TT *phT, TT *shT, int mode) {
+__global__ void __launch_bounds__(KT) bicgstab_kernel(KrylovArgs A, int mode) {
   const int nb = gridDim.x, bid = blockIdx.x;
   const int64_t n0 = (int64_t)bid * A.nnode / nb, n1 = (int64_t)(bid + 1) * A.nnode / nb;
   const int64_t r0 = ND * n0, r1 = ND * n1;
@@ -132,6 +134,7 @@ __global__ void __launch_bounds__(KT) bicgstab_kernel(KrylovArgs A, TT *phT, TT 
   int status = 1, it = 0;
   double rel = 0.0, bnorm = 0.0;
   double rho = 0.0, alpha = 1.0, omega = 1.0, rho_old = 1.0;
+  double best = 1.0;                           // best relative residual seen; xb holds its iterate
   bool ok = true;
 
   if (mode != 2) {
@@ -140,6 +143,7 @@ __global__ void __launch_bounds__(KT) bicgstab_kernel(KrylovArgs A, TT *phT, TT 
     for (int64_t row = r0 + threadIdx.x; row < r1; row += KT) {
       const double b = A.rhs[row];
       A.x[row] = 0.0;
+      A.xb[row] = 0.0;
       l += b * b;
     }
     publish(2, 0, l);
@@ -149,17 +153,17 @@ __global__ void __launch_bounds__(KT) bicgstab_kernel(KrylovArgs A, TT *phT, TT 
       if (!(bnorm > 0.0)) status = isfinite(bnorm) ? 0 : 3;
     }
     bool fresh = true, verify = false, first = true;
-    int restarts = 0;
+    int restarts = 0, since_best = 0;
     while (ok && bnorm > 0.0 && isfinite(bnorm)) {
       if (fresh) {
         // (re)start: r = b - K x (the true residual), shadow residual r0 = r
         if (restarts > 0) {
-          for (int64_t row = r0 + threadIdx.x; row < r1; row += KT) phT[row] = (TT)A.x[row];
+          for (int64_t row = r0 + threadIdx.x; row < r1; row += KT) A.ph[row] = A.x[row];
           if (!(ok = grid_barrier(A.bar_count, A.bar_gen, nb))) break;
         }
         double lrr = 0.0;
         for (int64_t row = r0 + threadIdx.x; row < r1; row += KT) {
-          const double rn = A.rhs[row] - (restarts > 0 ? spmv_row<ND, TT>(A.p, vals, phT, row) : 0.0);
+          const double rn = A.rhs[row] - (restarts > 0 ? spmv_row<ND, TT>(A.p, vals, A.ph, row) : 0.0);
           A.r[row] = rn;
           A.r0[row] = rn;
           A.pv[row] = 0.0;
@@ -171,6 +175,10 @@ __global__ void __launch_bounds__(KT) bicgstab_kernel(KrylovArgs A, TT *phT, TT 
         rho = grid_sum(part(2, 0), nb);
         rel = sqrt(rho) / bnorm;
         if (!isfinite(rho)) { status = 3; break; }
+        if (rel < best) {                       // the true residual of x: keep x as the best iterate
+          best = rel;
+          for (int64_t row = r0 + threadIdx.x; row < r1; row += KT) A.xb[row] = A.x[row];
+        }
         if (rel <= A.rtol) { status = 0; break; }
         if (verify && restarts >= KRYLOV_MAX_RESTARTS) { status = 1; break; }
         alpha = omega = rho_old = 1.0;
@@ -185,11 +193,11 @@ __global__ void __launch_bounds__(KT) bicgstab_kernel(KrylovArgs A, TT *phT, TT 
       for (int64_t row = r0 + threadIdx.x; row < r1; row += KT)
         A.pv[row] = A.r[row] + beta * (A.pv[row] - omega * A.v[row]);
       __syncthreads();
-      precond_rows<ND, TT>(minv, A.pv, A.ph, phT, r0, r1);
+      precond_rows<ND, TT>(minv, A.pv, A.ph, r0, r1);
       if (!(ok = grid_barrier(A.bar_count, A.bar_gen, nb))) break;
       double l1 = 0.0;
       for (int64_t row = r0 + threadIdx.x; row < r1; row += KT) {
-        const double vv = spmv_row<ND, TT>(A.p, vals, phT, row);
+        const double vv = spmv_row<ND, TT>(A.p, vals, A.ph, row);
         A.v[row] = vv;
         l1 += A.r0[row] * vv;
       }
@@ -206,11 +214,11 @@ __global__ void __launch_bounds__(KT) bicgstab_kernel(KrylovArgs A, TT *phT, TT 
       alpha = rho / r0v;
       for (int64_t row = r0 + threadIdx.x; row < r1; row += KT) A.sv[row] = A.r[row] - alpha * A.v[row];
       __syncthreads();
-      precond_rows<ND, TT>(minv, A.sv, A.sh, shT, r0, r1);
+      precond_rows<ND, TT>(minv, A.sv, A.sh, r0, r1);
       if (!(ok = grid_barrier(A.bar_count, A.bar_gen, nb))) break;
       double lts = 0.0, ltt = 0.0;
       for (int64_t row = r0 + threadIdx.x; row < r1; row += KT) {
-        const double tv = spmv_row<ND, TT>(A.p, vals, shT, row);
+        const double tv = spmv_row<ND, TT>(A.p, vals, A.sh, row);
         A.t[row] = tv;
         lts += tv * A.sv[row];
         ltt += tv * tv;
@@ -236,6 +244,14 @@ __global__ void __launch_bounds__(KT) bicgstab_kernel(KrylovArgs A, TT *phT, TT 
       rho = grid_sum(part(2, 1), nb);
       rel = sqrt(rr) / bnorm;
       if (!isfinite(rr)) { status = 3; break; }
+      if (rel < best) {
+        best = rel;
+        since_best = 0;
+        for (int64_t row = r0 + threadIdx.x; row < r1; row += KT) A.xb[row] = A.x[row];
+      } else if (++since_best > A.stall_iters) {   // no progress: stop with the best iterate
+        status = 1;
+        break;
+      }
       if (rel <= A.rtol || omega == 0.0 || rho == 0.0) {
         // recursive residual small, or breakdown: check the true residual
         // and restart from x when it is not small enough
@@ -245,6 +261,13 @@ __global__ void __launch_bounds__(KT) bicgstab_kernel(KrylovArgs A, TT *phT, TT 
         verify = rel <= A.rtol;
       }
     }
+  }
+  if (ok && mode != 2 && status != 0 && status != 3 && bnorm > 0.0) {
+    // not converged: return the best iterate (its recursive residual may be
+    // an underestimate of the true one by the drift BiCGSTAB accumulates)
+    __syncthreads();
+    for (int64_t row = r0 + threadIdx.x; row < r1; row += KT) A.x[row] = A.xb[row];
+    rel = best;
   }
   if (ok && mode != 0 && status != 3) {
     double ldu = 0.0, lu = 0.0, lde = 0.0, le = 0.0;
@@ -314,10 +337,9 @@ template int bicgstab_max_blocks<double>();
 template int bicgstab_max_blocks<float>();
 
 template <typename TT>
-cudaError_t launch_bicgstab(const KrylovArgs &a, void *phT, void *shT, int nblocks, int mode, cudaStream_t s) {
+cudaError_t launch_bicgstab(const KrylovArgs &a, int nblocks, int mode, cudaStream_t s) {
   KrylovArgs args = a;
-  TT *pT = static_cast<TT *>(phT), *sT = static_cast<TT *>(shT);
-  void *params[] = {&args, &pT, &sT, &mode};
+  void *params[] = {&args, &mode};
   const void *fn = nullptr;
   switch (a.nd) {
     case 2: fn = (const void *)bicgstab_kernel<2, TT>; break;
@@ -331,7 +353,7 @@ cudaError_t launch_bicgstab(const KrylovArgs &a, void *phT, void *shT, int nbloc
   if (e != cudaSuccess) return e;
   return cudaLaunchCooperativeKernel(fn, dim3(nblocks), dim3(KT), params, 0, s);
 }
-template cudaError_t launch_bicgstab<double>(const KrylovArgs &, void *, void *, int, int, cudaStream_t);
-template cudaError_t launch_bicgstab<float>(const KrylovArgs &, void *, void *, int, int, cudaStream_t);
+template cudaError_t launch_bicgstab<double>(const KrylovArgs &, int, int, cudaStream_t);
+template cudaError_t launch_bicgstab<float>(const KrylovArgs &, int, int, cudaStream_t);
 
 }  // namespace lgdm

@@ -94,6 +94,7 @@ cudaError_t launch_set_dirichlet(double *u, const int32_t *dof, const double *sc
                                  double load, cudaStream_t s);
 cudaError_t launch_commit(int elem, const MeshView &m, const double *u, double *kappa_hist,
                           cudaStream_t s);
+cudaError_t launch_fill(double *p, int64_t n, double v, cudaStream_t s);
 cudaError_t launch_damage_field(const MatConst &mc, const double *kappa_hist, int64_t n, double *out,
                                 cudaStream_t s);
 cudaError_t launch_reaction_sum(const double *re, const int32_t *idx, const double *w, int32_t n,
@@ -104,22 +105,21 @@ constexpr int KRYLOV_THREADS = 256;
 struct KrylovArgs {
   int32_t nd, nnode;
   int32_t max_iter;
-  int32_t pad;
+  int32_t stall_iters;        // stop after this many iterations without a new best residual
   double rtol, newton_tol;
   PatternView p;
   const void *vals;           // TT [nnz]
   const void *minv;           // TT [nnode*nd*nd]
   const double *rhs;          // [ndof]
-  double *x, *r, *r0, *pv, *v, *sv, *t, *ph, *sh;   // [ndof] each
+  double *x, *r, *r0, *pv, *v, *sv, *t, *ph, *sh, *xb;   // [ndof] each; xb = best iterate
   double *u;                  // [ndof] state (modes 1 and 2)
   double *partial;            // [3 slots][4 values][gridDim]
   unsigned int *bar_count, *bar_gen;
   SolveResult *res;
 };
 // mode 0: solve; 1: solve, u += delta, Newton test; 2: update and test only.
-// phT / shT: TT copies of the preconditioned vectors (may alias ph / sh for double).
 template <typename TT>
-cudaError_t launch_bicgstab(const KrylovArgs &a, void *phT, void *shT, int nblocks, int mode, cudaStream_t s);
+cudaError_t launch_bicgstab(const KrylovArgs &a, int nblocks, int mode, cudaStream_t s);
 template <typename TT>
 int bicgstab_max_blocks();
 

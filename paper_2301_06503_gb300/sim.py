@@ -120,6 +120,10 @@ class Sim:
             raise ValueError("kappa_hist must have nelem*ngp entries")
         self._ck(self._lib.lgdm_set_state(self.h, _p(u, C.c_double), _p(k, C.c_double)))
 
+    def reset_state(self):
+        """Back to u = 0, kappa_hist = kappa0 on the device (no re-creation)."""
+        self._ck(self._lib.lgdm_reset_state(self.h))
+
     def field(self, which) -> np.ndarray:
         which = {"u": L.FIELD_U, "kappa_hist": L.FIELD_KAPPA_HIST, "damage": L.FIELD_DAMAGE,
                  "delta": L.FIELD_DELTA, "residual": L.FIELD_RESIDUAL, "rhs": L.FIELD_RHS}.get(which, which)
@@ -174,6 +178,23 @@ class Sim:
         nrm = np.zeros(4)
         self._ck(self._lib.lgdm_last_solve(self.h, C.byref(it), C.byref(st), C.byref(rel), _p(nrm, C.c_double)))
         return int(it.value), int(st.value), float(rel.value), nrm
+
+    def enable_timers(self, on=True):
+        self._ck(self._lib.lgdm_enable_timers(self.h, 1 if on else 0))
+
+    def timers(self, reset=False):
+        """{phase: (milliseconds, launches)} from the CUDA-event phase timers."""
+        ms = np.zeros(L.NPHASES)
+        n = np.zeros(L.NPHASES, np.int64)
+        self._ck(self._lib.lgdm_get_timers(self.h, _p(ms, C.c_double), _p(n, C.c_int64)))
+        if reset:
+            self._ck(self._lib.lgdm_reset_timers(self.h))
+        return {name: (float(ms[k]), int(n[k])) for k, name in enumerate(L.PHASES)}
+
+    def counters(self):
+        c = np.zeros(6, np.int64)
+        self._ck(self._lib.lgdm_get_counters(self.h, _p(c, C.c_int64), 6))
+        return {name: int(c[k]) for k, name in enumerate(L.COUNTERS)}
 
     def reaction(self) -> float:
         r = C.c_double()
