@@ -219,6 +219,39 @@ lgdm_status lgdm_get_counters(const lgdm_sim *sim, int64_t *counters, int32_t n)
 /* Reaction at the last committed state.  Synchronises. */
 lgdm_status lgdm_get_reaction(lgdm_sim *sim, double *reaction);
 
+/* Solve K x = b by BiCGSTAB with node-block Jacobi, allocating nothing.
+ *
+ * For callers that cannot allocate device memory (a host framework that has
+ * reserved all of it, a plugin that must not touch the CUDA allocator): the
+ * working storage -- Krylov vectors, block inverses, partial sums, barrier
+ * words -- comes from one statically reserved 64 MiB device array held by
+ * every GPU that loads this library until the process exits.  The paper has
+ * no counterpart; this is the same solver as lgdm_solve on a caller-held
+ * system.
+ *
+ *   nd, nnode  dofs per node (2..4) and nodes; ndof = nd * nnode
+ *   nbr_ptr    device int32 [nnode+1]; nbr device int32 [nbr_ptr[nnode]]:
+ *              sorted neighbour nodes of every node, the node itself included
+ *   vals       device double, node-block CSR: row nd*a+i starts at
+ *              nd*nd*nbr_ptr[a] + i*nd*deg(a) and holds, for each neighbour
+ *              slot s, the nd columns nd*nbr[nbr_ptr[a]+s] + j (the order of
+ *              lgdm_get_system)
+ *   rhs, x     device double [ndof]; x receives the solution (x = 0 start)
+ *   rtol       stop when ||b - K x|| <= rtol ||b||; max_iter iteration cap
+ *   stream     cudaStream_t (NULL = default stream); the call synchronises it
+ *   iters, rel_res  may be NULL
+ *
+ * The first call on a device looks up the array's device address once, with
+ * that device current; make that first call before any stream capture.
+ * Systems whose scratch exceeds the array (about 80 bytes per dof) are
+ * rejected with LGDM_ERR_OOM and a message (lgdm_last_error(NULL)).  All
+ * calls share the array and it keeps the previous call's contents (the
+ * barrier words and the result are cleared at each call): calls that overlap
+ * on the GPU, from any thread or stream, race and must be serialised. */
+lgdm_status lgdm_solve_noalloc(int32_t nd, int32_t nnode, const int32_t *nbr_ptr, const int32_t *nbr,
+                               const double *vals, const double *rhs, double *x, double rtol,
+                               int32_t max_iter, void *stream, int32_t *iters, double *rel_res);
+
 #ifdef __cplusplus
 }
 #endif

@@ -84,6 +84,8 @@ _SIGS = {
     "lgdm_get_timers": (C.c_int, [C.c_void_p, _dp, C.POINTER(C.c_int64)]),
     "lgdm_reset_timers": (C.c_int, [C.c_void_p]),
     "lgdm_get_counters": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.c_int32]),
+    "lgdm_solve_noalloc": (C.c_int, [C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                     C.c_void_p, C.c_double, C.c_int32, C.c_void_p, _ip, _dp]),
 }
 
 _lib = None

@@ -187,6 +187,12 @@ struct lgdm_sim {
 
 namespace {
 
+}  // namespace
+
+void lgdm::set_global_error(const std::string &msg) { g_last_error = msg; }
+
+namespace {
+
 lgdm_status fail(lgdm_sim *s, lgdm_status st, const std::string &msg) {
   if (s) s->err = msg;
   else g_last_error = msg;

@@ -649,6 +649,19 @@ cudaError_t launch_fill(double *p, int64_t n, double v, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+__global__ void diag_pairs_kernel(PatternView p, int32_t *diag) {
+  const int32_t a = blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= p.nnode) return;
+  int32_t k = p.nbr_ptr[a];
+  const int32_t k1 = p.nbr_ptr[a + 1];
+  while (k < k1 && p.nbr[k] != a) ++k;
+  diag[a] = (k < k1) ? k : p.nbr_ptr[a];
+}
+cudaError_t launch_diag_pairs(const PatternView &p, int32_t *diag, cudaStream_t s) {
+  diag_pairs_kernel<<<(p.nnode + 255) / 256, 256, 0, s>>>(p, diag);
+  return cudaGetLastError();
+}
+
 __global__ void damage_field_kernel(MatConst mc, const double *kh, int64_t n, double *out) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;

@@ -2,6 +2,7 @@
 #pragma once
 #include <cstdint>
 #include <cstddef>
+#include <string>
 #include <cuda_runtime.h>
 #include "lgdm.h"
 
@@ -95,6 +96,10 @@ cudaError_t launch_set_dirichlet(double *u, const int32_t *dof, const double *sc
 cudaError_t launch_commit(int elem, const MeshView &m, const double *u, double *kappa_hist,
                           cudaStream_t s);
 cudaError_t launch_fill(double *p, int64_t n, double v, cudaStream_t s);
+// diag[a] = position of node a in its own neighbour list
+cudaError_t launch_diag_pairs(const PatternView &p, int32_t *diag, cudaStream_t s);
+// message for lgdm_last_error(NULL)
+void set_global_error(const std::string &msg);
 cudaError_t launch_damage_field(const MatConst &mc, const double *kappa_hist, int64_t n, double *out,
                                 cudaStream_t s);
 cudaError_t launch_reaction_sum(const double *re, const int32_t *idx, const double *w, int32_t n,

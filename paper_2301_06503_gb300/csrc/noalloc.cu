@@ -1,0 +1,132 @@
+// Allocation-free BiCGSTAB solve of a node-block CSR system.
+//
+// Some callers cannot allocate device memory at all: code that runs inside
+// a host framework whose memory is fully pre-reserved, callers holding a
+// captured-allocation budget, or plugins that must not touch the CUDA
+// allocator.  For them lgdm_solve_noalloc takes its working storage from one
+// file-scope __device__ array instead of a workspace: the caller passes only
+// the system (inputs) and the solution buffer (output).
+//
+// The array is reserved when the library is loaded, on every GPU that loads
+// it, and stays reserved until the process exits.  Host code cannot use the
+// array's name as a device address; at the first call on a device, with that
+// device current, its address is fetched once with cudaGetSymbolAddress and
+// cached per device.
+#include "lgdm_internal.cuh"
+
+#include <algorithm>
+#include <mutex>
+#include <string>
+
+namespace lgdm {
+
+constexpr size_t NOALLOC_SCRATCH_BYTES = size_t(64) << 20;   // 64 MiB
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
+
+namespace {
+
+constexpr int MAX_DEVICES = 64;
+std::mutex g_mu;
+void *g_addr[MAX_DEVICES] = {};
+size_t up256(size_t n) { return (n + 255) & ~size_t(255); }
+
+lgdm_status err(lgdm_status s, const std::string &m) {
+  set_global_error(m);
+  return s;
+}
+
+}  // namespace
+}  // namespace lgdm
+
+using namespace lgdm;
+
+extern "C" lgdm_status lgdm_solve_noalloc(int32_t nd, int32_t nnode, const int32_t *nbr_ptr, const int32_t *nbr,
+                                          const double *vals, const double *rhs, double *x, double rtol,
+                                          int32_t max_iter, void *stream, int32_t *iters, double *rel_res) {
+  if (nd < 2 || nd > 4 || nnode <= 0 || !nbr_ptr || !nbr || !vals || !rhs || !x || !(rtol > 0.0) || max_iter < 1)
+    return err(LGDM_ERR_INVALID_ARG, "bad argument");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEVICES)
+    return err(LGDM_ERR_CUDA, "no current CUDA device");
+  void *base = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!g_addr[dev]) {
+      void *p = nullptr;
+      const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+      if (e != cudaSuccess) return err(LGDM_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+      g_addr[dev] = p;
+    }
+    base = g_addr[dev];
+  }
+  const int nblocks_max = bicgstab_max_blocks<double>();
+  const int64_t ndof = (int64_t)nd * nnode;
+  int nb = (int)std::min<int64_t>((ndof + 2 * KRYLOV_THREADS - 1) / (2 * KRYLOV_THREADS), nblocks_max);
+  if (nb < 1) nb = 1;
+  // layout inside the static array
+  const size_t vec = up256(sizeof(double) * ndof);
+  const size_t need = 9 * vec + up256(sizeof(double) * nnode * nd * nd) + up256(sizeof(double) * 12 * nb) +
+                      up256(2 * sizeof(unsigned int)) + up256(sizeof(SolveResult)) + up256(sizeof(int32_t) * nnode);
+  if (need > NOALLOC_SCRATCH_BYTES)
+    return err(LGDM_ERR_OOM, "system needs " + std::to_string(need) + " bytes of scratch; the static array holds " +
+                                 std::to_string(NOALLOC_SCRATCH_BYTES));
+  char *c = static_cast<char *>(base);
+  double *v[9];
+  for (int k = 0; k < 9; ++k, c += vec) v[k] = reinterpret_cast<double *>(c);
+  double *minv = reinterpret_cast<double *>(c);
+  c += up256(sizeof(double) * nnode * nd * nd);
+  double *partial = reinterpret_cast<double *>(c);
+  c += up256(sizeof(double) * 12 * nb);
+  unsigned int *bar = reinterpret_cast<unsigned int *>(c);
+  c += up256(2 * sizeof(unsigned int));
+  SolveResult *res = reinterpret_cast<SolveResult *>(c);
+  c += up256(sizeof(SolveResult));
+  int32_t *diag = reinterpret_cast<int32_t *>(c);
+
+  PatternView p{};
+  p.nnode = nnode;
+  p.nbr_ptr = nbr_ptr;
+  p.nbr = nbr;
+  p.diag_pair = diag;
+  cudaError_t e = launch_diag_pairs(p, diag, s);
+  if (e == cudaSuccess) e = launch_precond<double>(nd, p, vals, LGDM_PRECOND_NODE_BLOCK, minv, s);
+  if (e != cudaSuccess) return err(LGDM_ERR_CUDA, std::string("set-up: ") + cudaGetErrorString(e));
+  KrylovArgs a{};
+  a.nd = nd;
+  a.nnode = nnode;
+  a.max_iter = max_iter;
+  a.stall_iters = std::max(500, max_iter / 4);
+  a.rtol = rtol;
+  a.newton_tol = 0.0;
+  a.p = p;
+  a.vals = vals;
+  a.minv = minv;
+  a.rhs = rhs;
+  a.x = x;
+  a.r = v[0];
+  a.r0 = v[1];
+  a.pv = v[2];
+  a.v = v[3];
+  a.sv = v[4];
+  a.t = v[5];
+  a.ph = v[6];
+  a.sh = v[7];
+  a.xb = v[8];
+  a.u = nullptr;
+  a.partial = partial;
+  a.bar_count = bar;
+  a.bar_gen = bar + 1;
+  a.res = res;
+  e = launch_bicgstab<double>(a, nb, 0, s);
+  if (e != cudaSuccess) return err(LGDM_ERR_CUDA, std::string("launch: ") + cudaGetErrorString(e));
+  SolveResult out{};
+  e = cudaMemcpyAsync(&out, res, sizeof(SolveResult), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return err(LGDM_ERR_CUDA, std::string("sync: ") + cudaGetErrorString(e));
+  if (iters) *iters = out.iters;
+  if (rel_res) *rel_res = out.rel_res;
+  if (out.status == 4) return err(LGDM_ERR_TIMEOUT, "grid barrier timed out");
+  if (out.status == 3) return err(LGDM_ERR_NONFINITE, "non-finite value in the solve");
+  return LGDM_OK;
+}
