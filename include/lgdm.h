@@ -109,6 +109,8 @@ typedef struct {
   int32_t max_krylov;         /* BiCGSTAB iterations per solve                    */
   int32_t max_halvings;       /* load-increment halvings before giving up         */
   int32_t krylov_blocks;      /* 0 = as many co-resident blocks as fit            */
+  int32_t gmres_m;            /* restart of GMRES (1..128); 0 = no GMRES          */
+  int32_t krylov_method;      /* 0 BiCGSTAB, GMRES when it falls short; 1 GMRES    */
 } lgdm_options;
 
 typedef struct lgdm_sim lgdm_sim;
@@ -125,7 +127,8 @@ int32_t lgdm_abi_version(void);
 const char *lgdm_status_string(lgdm_status s);
 
 /* Fill *opt with the defaults (FP64, node-block Jacobi, tol 1e-8, rtol 1e-8,
- * 50 Newton iterations, 5000 Krylov iterations, 6 halvings). */
+ * 50 Newton iterations, 5000 Krylov iterations, 6 halvings, GMRES(64)
+ * fallback). */
 lgdm_status lgdm_default_options(lgdm_options *opt);
 
 /* Device workspace bytes the simulation of this mesh needs.  Builds the node
@@ -179,8 +182,10 @@ lgdm_status lgdm_solve(lgdm_sim *sim, int32_t *iters, double *rel_res);
 /* u += delta and the convergence test of Algorithm 2, line 18.  Synchronises. */
 lgdm_status lgdm_update(lgdm_sim *sim, int32_t *converged);
 
-/* One Newton iteration: assemble, then one persistent launch that solves,
- * updates and tests convergence.  Synchronises once. */
+/* One Newton iteration: assemble, solve (BiCGSTAB; when it does not reach
+ * krylov_rtol, restarted GMRES continues from its best iterate), then the
+ * update and the convergence test.  The increment is accepted as converged
+ * only if its linear solve reached a relative residual of 1e-3 or less. */
 lgdm_status lgdm_newton_step(lgdm_sim *sim, int32_t *converged, int32_t *krylov_iters);
 
 /* One load step to `load`: begin_step, Newton iterations until convergence,

@@ -42,7 +42,8 @@ class BCs(C.Structure):
 class Options(C.Structure):
     _fields_ = [("precision", C.c_int32), ("precond", C.c_int32), ("newton_tol", C.c_double),
                 ("krylov_rtol", C.c_double), ("max_newton", C.c_int32), ("max_krylov", C.c_int32),
-                ("max_halvings", C.c_int32), ("krylov_blocks", C.c_int32)]
+                ("max_halvings", C.c_int32), ("krylov_blocks", C.c_int32), ("gmres_m", C.c_int32),
+                ("krylov_method", C.c_int32)]
 
 
 class Sizes(C.Structure):

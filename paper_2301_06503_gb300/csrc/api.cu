@@ -150,7 +150,10 @@ struct lgdm_sim {
   double *u = nullptr, *u_commit = nullptr, *kappa_hist = nullptr;
   void *Ke = nullptr, *vals = nullptr, *minv = nullptr;
   double *re = nullptr, *rraw = nullptr, *rhs = nullptr;
-  double *kv[10] = {};
+  double *kv[11] = {};
+  double *gm_V = nullptr, *gm_R = nullptr, *gm_y = nullptr, *gm_dots = nullptr, *gm_final = nullptr;
+  int64_t gm_ld = 0;
+  int gmres_blocks = 1;
   double *partial = nullptr, *field_tmp = nullptr, *reaction = nullptr;
   unsigned int *bar = nullptr;
   SolveResult *res = nullptr;
@@ -292,7 +295,16 @@ void carve(lgdm_sim &s, Carver &c) {
   s.minv = c.take<char>((size_t)s.nnode * s.nd * s.nd * s.tsize);
   s.rraw = c.take<double>(s.ndof);
   s.rhs = c.take<double>(s.ndof);
-  for (int k = 0; k < 10; ++k) s.kv[k] = c.take<double>(s.ndof);
+  for (int k = 0; k < 11; ++k) s.kv[k] = c.take<double>(s.ndof);
+  if (s.opt.gmres_m > 0) {
+    const int m = s.opt.gmres_m;
+    s.gm_ld = (s.ndof + 31) & ~int64_t(31);
+    s.gm_V = c.take<double>((size_t)(m + 1) * s.gm_ld);
+    s.gm_R = c.take<double>((size_t)m * (m + 1));
+    s.gm_y = c.take<double>(m);
+    s.gm_dots = c.take<double>((size_t)(GMRES_MAX_M + 2) * std::max(s.gmres_blocks, 1));
+    s.gm_final = c.take<double>(m + 2);
+  }
   s.partial = c.take<double>((size_t)3 * 4 * std::max(s.krylov_blocks, 1));
   s.field_tmp = c.take<double>(std::max((size_t)s.nel * s.ngp, (size_t)s.ndof));
   s.reaction = c.take<double>(1);
@@ -343,6 +355,11 @@ lgdm_status plan(lgdm_sim &s, const lgdm_mesh &m, const lgdm_options &o, const l
   s.ncontrib = (int64_t)s.nel * s.nen * s.nen;
   s.ndir = bcs ? bcs->n_dir : 0;
   s.krylov_blocks = choose_krylov_blocks(s, query_device);
+  s.gmres_blocks = s.krylov_blocks;
+  if (query_device && o.gmres_m > 0) {
+    const int cap = (o.precision == LGDM_PREC_FP32_TANGENT) ? gmres_max_blocks<float>() : gmres_max_blocks<double>();
+    if (cap > 0) s.gmres_blocks = std::min(s.gmres_blocks, cap);
+  }
   return LGDM_OK;
 }
 
@@ -377,6 +394,8 @@ lgdm_status lgdm_default_options(lgdm_options *o) {
   o->max_krylov = 5000;
   o->max_halvings = 6;
   o->krylov_blocks = 0;
+  o->gmres_m = 64;
+  o->krylov_method = 0;
   return LGDM_OK;
 }
 
@@ -394,6 +413,7 @@ lgdm_status lgdm_workspace_size(const lgdm_mesh *m, const lgdm_options *o, size_
     s.n_reac_elems = s.nel;
     s.n_reac = (int32_t)std::min<int64_t>((int64_t)s.nel * s.nen * s.nd, INT32_MAX);
     s.krylov_blocks = 152 * 16;
+    s.gmres_blocks = 152 * 16;
     Carver c{nullptr};
     carve(s, c);
     *bytes = s.ws_needed;
@@ -419,6 +439,10 @@ lgdm_status lgdm_create(const lgdm_mesh *m, const lgdm_material *mat, const lgdm
       return fail(nullptr, LGDM_ERR_INVALID_ARG, "unknown precision");
     if (o->max_newton < 1 || o->max_krylov < 1 || o->max_halvings < 0 || !(o->newton_tol > 0.0))
       return fail(nullptr, LGDM_ERR_INVALID_ARG, "bad iteration limits or tolerance");
+    if (o->gmres_m < 0 || o->gmres_m > GMRES_MAX_M)
+      return fail(nullptr, LGDM_ERR_INVALID_ARG, "gmres_m must be in 0..128");
+    if (o->krylov_method != 0 && !(o->krylov_method == 1 && o->gmres_m > 0))
+      return fail(nullptr, LGDM_ERR_INVALID_ARG, "krylov_method 1 (GMRES) needs gmres_m > 0");
     if (bcs && bcs->n_dir > 0 && (!bcs->dir_dof || !bcs->dir_scale))
       return fail(nullptr, LGDM_ERR_INVALID_ARG, "Dirichlet arrays missing");
     s = new lgdm_sim();
@@ -702,6 +726,7 @@ KrylovArgs krylov_args(lgdm_sim *s) {
   a.ph = s->kv[7];
   a.sh = s->kv[8];
   a.xb = s->kv[9];
+  a.prior_rel = s->last.rel_res;
   a.stall_iters = std::max(500, s->opt.max_krylov / 4);
   a.u = s->u;
   a.partial = s->partial;
@@ -711,15 +736,7 @@ KrylovArgs krylov_args(lgdm_sim *s) {
   return a;
 }
 
-lgdm_status run_krylov(lgdm_sim *s, int mode, SolveResult *out) {
-  const KrylovArgs a = krylov_args(s);
-  {
-    PhaseTimer pt(s, 3);
-    if (s->opt.precision == LGDM_PREC_FP32_TANGENT)
-      LGDM_CUDA(s, launch_bicgstab<float>(a, s->krylov_blocks, mode, s->stream));
-    else
-      LGDM_CUDA(s, launch_bicgstab<double>(a, s->krylov_blocks, mode, s->stream));
-  }
+lgdm_status finish_launch(lgdm_sim *s, int mode, SolveResult *out) {
   s->counters[0] += 1;
   LGDM_CUDA(s, cudaMemcpyAsync(out, s->res, sizeof(SolveResult), cudaMemcpyDeviceToHost, s->stream));
   LGDM_CUDA(s, cudaStreamSynchronize(s->stream));
@@ -736,6 +753,63 @@ lgdm_status run_krylov(lgdm_sim *s, int mode, SolveResult *out) {
   return LGDM_OK;
 }
 
+lgdm_status run_krylov(lgdm_sim *s, int mode, SolveResult *out) {
+  const KrylovArgs a = krylov_args(s);
+  {
+    PhaseTimer pt(s, 3);
+    if (s->opt.precision == LGDM_PREC_FP32_TANGENT)
+      LGDM_CUDA(s, launch_bicgstab<float>(a, s->krylov_blocks, mode, s->stream));
+    else
+      LGDM_CUDA(s, launch_bicgstab<double>(a, s->krylov_blocks, mode, s->stream));
+  }
+  return finish_launch(s, mode, out);
+}
+
+// GMRES from the x left by the previous solve.
+lgdm_status run_gmres(lgdm_sim *s, SolveResult *out) {
+  const KrylovArgs a = krylov_args(s);
+  GmresArgs g{};
+  g.m = s->opt.gmres_m;
+  g.ld = s->gm_ld;
+  g.V = s->gm_V;
+  g.R = s->gm_R;
+  g.y = s->gm_y;
+  g.dots = s->gm_dots;
+  g.final = s->gm_final;
+  g.xs = s->kv[10];
+  {
+    PhaseTimer pt(s, 3);
+    if (s->opt.precision == LGDM_PREC_FP32_TANGENT)
+      LGDM_CUDA(s, launch_gmres<float>(a, g, s->gmres_blocks, s->stream));
+    else
+      LGDM_CUDA(s, launch_gmres<double>(a, g, s->gmres_blocks, s->stream));
+  }
+  return finish_launch(s, 0, out);
+}
+
+// Solve with BiCGSTAB, continue with GMRES when it falls short of krylov_rtol.
+lgdm_status solve_robust(lgdm_sim *s, SolveResult *out) {
+  if (s->opt.krylov_method == 1) {
+    LGDM_CUDA(s, cudaMemsetAsync(s->kv[0], 0, sizeof(double) * s->ndof, s->stream));
+    return run_gmres(s, out);
+  }
+  lgdm_status st = run_krylov(s, 0, out);
+  if (st != LGDM_OK && st != LGDM_ERR_NONFINITE) return st;
+  // hand over to GMRES only when BiCGSTAB ended far from its tolerance
+  const bool short_of = (st == LGDM_ERR_NONFINITE) || (out->status != 0 && out->rel_res > 1e3 * s->opt.krylov_rtol);
+  if (!short_of || s->opt.gmres_m <= 0) return st;
+  const int32_t bicg_iters = out->iters;
+  if (st == LGDM_ERR_NONFINITE)
+    LGDM_CUDA(s, cudaMemsetAsync(s->kv[0], 0, sizeof(double) * s->ndof, s->stream));
+  else
+    LGDM_CUDA(s, cudaMemcpyAsync(s->kv[0], s->kv[9], sizeof(double) * s->ndof, cudaMemcpyDeviceToDevice,
+                                 s->stream));   // best BiCGSTAB iterate
+  st = run_gmres(s, out);
+  out->iters += bicg_iters;
+  s->last.iters = out->iters;
+  return st;
+}
+
 }  // namespace
 
 extern "C" {
@@ -744,7 +818,7 @@ lgdm_status lgdm_solve(lgdm_sim *s, int32_t *iters, double *rel_res) {
   if (!s) return fail(nullptr, LGDM_ERR_INVALID_ARG, "NULL handle");
   if (!s->assembled) return fail(s, LGDM_ERR_STATE, "solve before assemble");
   SolveResult r{};
-  lgdm_status st = run_krylov(s, 0, &r);
+  lgdm_status st = solve_robust(s, &r);
   if (iters) *iters = r.iters;
   if (rel_res) *rel_res = r.rel_res;
   return st;
@@ -763,10 +837,14 @@ lgdm_status lgdm_newton_step(lgdm_sim *s, int32_t *converged, int32_t *krylov_it
   lgdm_status st = lgdm_assemble(s);
   if (st != LGDM_OK) return st;
   SolveResult r{};
-  st = run_krylov(s, 1, &r);
+  st = solve_robust(s, &r);
+  if (st != LGDM_OK) return st;
+  const int32_t its = r.iters;
+  SolveResult u{};
+  st = run_krylov(s, 2, &u);
   s->assembled = false;
-  if (converged) *converged = r.converged;
-  if (krylov_iters) *krylov_iters = r.iters;
+  if (converged) *converged = u.converged;
+  if (krylov_iters) *krylov_iters = its;
   return st;
 }
 

@@ -22,6 +22,9 @@ namespace lgdm {
 constexpr int KT = KRYLOV_THREADS;
 constexpr unsigned long long BARRIER_NS = 2000000000ull;   // 2 s
 constexpr int KRYLOV_MAX_RESTARTS = 8;
+// Largest relative linear residual with which a Newton increment may still be
+// accepted as the converged one (an inexact-Newton forcing term).
+constexpr double KRYLOV_NEWTON_ETA = 1e-3;
 
 __device__ __forceinline__ unsigned long long globaltimer() {
   unsigned long long t;
@@ -111,10 +114,10 @@ __device__ __forceinline__ void precond_rows(const TT *__restrict__ minv, const 
     const int i = (int)(row % ND);
     const TT *m = minv + (a * ND + i) * ND;
     const double *x = in + a * ND;
-    TT s = (TT)0;
+    double s = 0.0;                 // stored in TT, applied in double: a linear preconditioner
 #pragma unroll
-    for (int j = 0; j < ND; ++j) s += m[j] * (TT)x[j];
-    out[row] = (double)s;
+    for (int j = 0; j < ND; ++j) s += (double)m[j] * x[j];
+    out[row] = s;
   }
 }
 
@@ -297,7 +300,8 @@ __global__ void __launch_bounds__(KT) bicgstab_kernel(KrylovArgs A, int mode) {
         const bool ce = nrm[3] > 0.0 ? nrm[2] <= A.newton_tol * nrm[3] : nrm[2] <= 1e-30;
         // a stalled or broken-down solve can return a tiny increment: never
         // accept it as convergence
-        const bool solved = (mode == 2) || status == 0 || rel <= 100.0 * A.rtol;
+        const bool solved = (mode == 2) ? (A.prior_rel <= KRYLOV_NEWTON_ETA)
+                                        : (status == 0 || rel <= KRYLOV_NEWTON_ETA);
         A.res->converged = (cu && ce && solved) ? 1 : 0;
 #pragma unroll
         for (int k = 0; k < 4; ++k) A.res->norms[k] = nrm[k];
@@ -355,5 +359,272 @@ cudaError_t launch_bicgstab(const KrylovArgs &a, int nblocks, int mode, cudaStre
 }
 template cudaError_t launch_bicgstab<double>(const KrylovArgs &, int, int, cudaStream_t);
 template cudaError_t launch_bicgstab<float>(const KrylovArgs &, int, int, cudaStream_t);
+
+// ====================================================================== GMRES
+// Restarted GMRES(m), right-preconditioned by the node-block Jacobi inverse,
+// classical Gram-Schmidt with one re-orthogonalisation pass.  It is the
+// fallback when BiCGSTAB stagnates or diverges on an indefinite tangent:
+// GMRES never increases the residual within a cycle.  Warm start from the
+// x already in A.x.  Inner products against the basis are computed
+// warp-per-vector over each block's rows, published per block, reduced by
+// one block per value, then read by all: every block sees the same numbers.
+namespace {
+
+template <int ND, typename TT>
+__device__ void gm_residual(const KrylovArgs &A, const GmresArgs &G, int64_t r0, int64_t r1, double *rout,
+                            double *lsq) {
+  // rout = b - K x (x copied to the scratch vector first: other blocks read it)
+  double l = 0.0;
+  for (int64_t row = r0 + threadIdx.x; row < r1; row += KT) {
+    const double rn = A.rhs[row] - spmv_row<ND, TT>(A.p, static_cast<const TT *>(A.vals), G.xs, row);
+    rout[row] = rn;
+    l += rn * rn;
+  }
+  *lsq = l;
+}
+
+}  // namespace
+
+template <int ND, typename TT>
+__global__ void __launch_bounds__(KT) gmres_kernel(KrylovArgs A, GmresArgs G) {
+  const int nb = gridDim.x, bid = blockIdx.x;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  constexpr int NW = KT / 32;
+  const int64_t n0 = (int64_t)bid * A.nnode / nb, n1 = (int64_t)(bid + 1) * A.nnode / nb;
+  const int64_t r0 = ND * n0, r1 = ND * n1;
+  const int64_t ld = G.ld;
+  const int m = G.m;
+  const TT *minv = static_cast<const TT *>(A.minv);
+  double *V = G.V;
+  __shared__ double s_h[GMRES_MAX_M + 2], s_h2[GMRES_MAX_M + 2];
+  __shared__ double s_cs[GMRES_MAX_M], s_sn[GMRES_MAX_M], s_g[GMRES_MAX_M + 1];
+  __shared__ int s_k;
+  auto part = [&](int i) { return G.dots + (int64_t)i * nb; };
+  // block-sum of one value per thread, published as partial i
+  auto publish = [&](int i, double v) {
+    const double s = block_sum(v);
+    if (threadIdx.x == 0) __stcg(part(i) + bid, s);
+  };
+  // one block per value sums the nb partials of values 0..cnt-1 into G.final
+  auto reduce = [&](int cnt) {
+    for (int i = bid; i < cnt; i += nb) {
+      const double s = grid_sum(part(i), nb);
+      if (threadIdx.x == 0) __stcg(G.final + i, s);
+    }
+  };
+  bool ok = true;
+  int status = 1, it = 0;
+  double bnorm = 0.0, rel = 1.0;
+  // ||b||
+  {
+    double l = 0.0;
+    for (int64_t row = r0 + threadIdx.x; row < r1; row += KT) l += A.rhs[row] * A.rhs[row];
+    publish(0, l);
+    for (int64_t row = r0 + threadIdx.x; row < r1; row += KT) G.xs[row] = A.x[row];
+    ok = grid_barrier(A.bar_count, A.bar_gen, nb);
+    if (ok) bnorm = sqrt(grid_sum(part(0), nb));
+  }
+  if (ok && !(bnorm > 0.0)) status = isfinite(bnorm) ? 0 : 3;
+  double prev_cycle = 1e300;
+  for (int cycle = 0; ok && bnorm > 0.0 && isfinite(bnorm); ++cycle) {
+    // true residual of the current x
+    double l;
+    gm_residual<ND, TT>(A, G, r0, r1, V, &l);            // V_0 <- r (unnormalised)
+    publish(0, l);
+    if (!(ok = grid_barrier(A.bar_count, A.bar_gen, nb))) break;
+    const double beta = sqrt(grid_sum(part(0), nb));
+    rel = beta / bnorm;
+    if (!isfinite(beta)) { status = 3; break; }
+    if (rel <= A.rtol) { status = 0; break; }
+    if (rel >= prev_cycle) {
+      // the cycle made the true residual worse (rounding in an ill-conditioned
+      // least-squares update): return the previous iterate
+      for (int64_t row = r0 + threadIdx.x; row < r1; row += KT) A.x[row] = A.xb[row];
+      rel = prev_cycle;
+      status = 1;
+      break;
+    }
+    for (int64_t row = r0 + threadIdx.x; row < r1; row += KT) A.xb[row] = A.x[row];
+    if (it >= A.max_iter) { status = 1; break; }
+    if (rel > 0.999 * prev_cycle) { status = 1; break; }    // a whole cycle without progress
+    prev_cycle = rel;
+    for (int64_t row = r0 + threadIdx.x; row < r1; row += KT) V[row] /= beta;
+    if (threadIdx.x == 0) {
+      s_g[0] = beta;
+      for (int i = 1; i <= m; ++i) s_g[i] = 0.0;
+    }
+    int k = 0;
+    for (int j = 0; j < m && it < A.max_iter; ++j) {
+      ++it;
+      const double *Vj = V + j * ld;
+      double *W = V + (j + 1) * ld;
+      // z = M^-1 V_j (node-local), into the scratch vector read by the SpMV
+      for (int64_t row = r0 + threadIdx.x; row < r1; row += KT) {
+        const int64_t a = row / ND;
+        const int i = (int)(row % ND);
+        const TT *mm = minv + (a * ND + i) * ND;
+        double s = 0.0;
+#pragma unroll
+        for (int q = 0; q < ND; ++q) s += (double)mm[q] * Vj[a * ND + q];
+        G.xs[row] = s;
+      }
+      if (!(ok = grid_barrier(A.bar_count, A.bar_gen, nb))) break;
+      for (int64_t row = r0 + threadIdx.x; row < r1; row += KT)
+        W[row] = spmv_row<ND, TT>(A.p, static_cast<const TT *>(A.vals), G.xs, row);
+      __syncthreads();
+      // pass 1: h_i = (V_i, w)
+      for (int i = warp; i <= j; i += NW) {
+        const double *Vi = V + i * ld;
+        double s = 0.0;
+        for (int64_t row = r0 + lane; row < r1; row += 32) s += Vi[row] * W[row];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) __stcg(part(i) + bid, s);
+      }
+      if (!(ok = grid_barrier(A.bar_count, A.bar_gen, nb))) break;
+      reduce(j + 1);
+      if (!(ok = grid_barrier(A.bar_count, A.bar_gen, nb))) break;
+      for (int i = threadIdx.x; i <= j; i += KT) s_h[i] = __ldcg(G.final + i);
+      __syncthreads();
+      for (int64_t row = r0 + threadIdx.x; row < r1; row += KT) {
+        double s = 0.0;
+        for (int i = 0; i <= j; ++i) s += s_h[i] * V[i * ld + row];
+        W[row] -= s;
+      }
+      __syncthreads();
+      // pass 2 (re-orthogonalisation)
+      for (int i = warp; i <= j; i += NW) {
+        const double *Vi = V + i * ld;
+        double s = 0.0;
+        for (int64_t row = r0 + lane; row < r1; row += 32) s += Vi[row] * W[row];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) __stcg(part(i) + bid, s);
+      }
+      if (!(ok = grid_barrier(A.bar_count, A.bar_gen, nb))) break;
+      reduce(j + 1);
+      if (!(ok = grid_barrier(A.bar_count, A.bar_gen, nb))) break;
+      for (int i = threadIdx.x; i <= j; i += KT) s_h2[i] = __ldcg(G.final + i);
+      __syncthreads();
+      // ||w|| after both passes, computed directly (a Pythagorean update
+      // cancels when the new direction is nearly in the span)
+      double lw = 0.0;
+      for (int64_t row = r0 + threadIdx.x; row < r1; row += KT) {
+        double s = 0.0;
+        for (int i = 0; i <= j; ++i) s += s_h2[i] * V[i * ld + row];
+        const double wn = W[row] - s;
+        W[row] = wn;
+        lw += wn * wn;
+      }
+      publish(GMRES_MAX_M + 1, lw);
+      if (!(ok = grid_barrier(A.bar_count, A.bar_gen, nb))) break;
+      const double hnext = sqrt(grid_sum(part(GMRES_MAX_M + 1), nb));
+      for (int64_t row = r0 + threadIdx.x; row < r1; row += KT) W[row] = (hnext > 0.0) ? W[row] / hnext : 0.0;
+      // Hessenberg column, previous rotations, new rotation (same in every block)
+      if (threadIdx.x == 0) {
+        double col[GMRES_MAX_M + 1];
+        for (int i = 0; i <= j; ++i) col[i] = s_h[i] + s_h2[i];
+        col[j + 1] = hnext;
+        for (int i = 0; i < j; ++i) {
+          const double t = s_cs[i] * col[i] + s_sn[i] * col[i + 1];
+          col[i + 1] = -s_sn[i] * col[i] + s_cs[i] * col[i + 1];
+          col[i] = t;
+        }
+        const double den = sqrt(col[j] * col[j] + col[j + 1] * col[j + 1]);
+        const double c = den > 0.0 ? col[j] / den : 1.0, sn = den > 0.0 ? col[j + 1] / den : 0.0;
+        s_cs[j] = c;
+        s_sn[j] = sn;
+        col[j] = den;
+        s_g[j + 1] = -sn * s_g[j];
+        s_g[j] = c * s_g[j];
+        if (bid == 0)
+          for (int i = 0; i <= j; ++i) G.R[(int64_t)j * (m + 1) + i] = col[i];
+        s_k = j + 1;
+      }
+      __syncthreads();
+      k = s_k;
+      rel = fabs(s_g[k]) / bnorm;
+      if (!isfinite(rel)) { status = 3; break; }
+      if (rel <= A.rtol || hnext == 0.0) break;
+    }
+    if (!ok || status == 3) break;
+    // x += M^-1 V_k y with R y = g (back substitution in block 0)
+    if (!(ok = grid_barrier(A.bar_count, A.bar_gen, nb))) break;
+    if (bid == 0 && threadIdx.x == 0) {
+      for (int i = k - 1; i >= 0; --i) {
+        double s = s_g[i];
+        for (int q = i + 1; q < k; ++q) s -= __ldcg(G.R + (int64_t)q * (m + 1) + i) * G.y[q];
+        const double d = __ldcg(G.R + (int64_t)i * (m + 1) + i);
+        G.y[i] = (d != 0.0) ? s / d : 0.0;
+      }
+    }
+    if (!(ok = grid_barrier(A.bar_count, A.bar_gen, nb))) break;
+    for (int64_t row = r0 + threadIdx.x; row < r1; row += KT) {
+      double s = 0.0;
+      for (int i = 0; i < k; ++i) s += __ldcg(G.y + i) * V[i * ld + row];
+      A.t[row] = s;
+    }
+    __syncthreads();
+    for (int64_t row = r0 + threadIdx.x; row < r1; row += KT) {
+      const int64_t a = row / ND;
+      const int i = (int)(row % ND);
+      const TT *mm = minv + (a * ND + i) * ND;
+      double s = 0.0;
+#pragma unroll
+      for (int q = 0; q < ND; ++q) s += (double)mm[q] * A.t[a * ND + q];
+      A.x[row] += s;
+      G.xs[row] = A.x[row];
+    }
+    if (!(ok = grid_barrier(A.bar_count, A.bar_gen, nb))) break;
+  }
+  if (!ok) {
+    if (threadIdx.x == 0) atomicMax(&A.res->status, 4);
+    return;
+  }
+  if (bid == 0 && threadIdx.x == 0) {
+    A.res->iters = it;
+    A.res->rel_res = rel;
+    A.res->bnorm = bnorm;
+    atomicMax(&A.res->status, status);
+  }
+}
+
+template <typename TT>
+int gmres_max_blocks() {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  int p2 = 0, p3 = 0, p4 = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p2, gmres_kernel<2, TT>, KT, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p3, gmres_kernel<3, TT>, KT, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p4, gmres_kernel<4, TT>, KT, 0);
+  int per = p2 < p3 ? p2 : p3;
+  per = per < p4 ? per : p4;
+  return per * sms;
+}
+template int gmres_max_blocks<double>();
+template int gmres_max_blocks<float>();
+
+template <typename TT>
+cudaError_t launch_gmres(const KrylovArgs &a, const GmresArgs &g, int nblocks, cudaStream_t s) {
+  if (g.m < 1 || g.m > GMRES_MAX_M) return cudaErrorInvalidValue;
+  KrylovArgs args = a;
+  GmresArgs gg = g;
+  void *params[] = {&args, &gg};
+  const void *fn = nullptr;
+  switch (a.nd) {
+    case 2: fn = (const void *)gmres_kernel<2, TT>; break;
+    case 3: fn = (const void *)gmres_kernel<3, TT>; break;
+    case 4: fn = (const void *)gmres_kernel<4, TT>; break;
+    default: return cudaErrorInvalidValue;
+  }
+  cudaError_t e = cudaMemsetAsync(a.bar_count, 0, 2 * sizeof(unsigned int), s);
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(&a.res->status, 0, sizeof(int32_t), s);
+  if (e != cudaSuccess) return e;
+  return cudaLaunchCooperativeKernel(fn, dim3(nblocks), dim3(KT), params, 0, s);
+}
+template cudaError_t launch_gmres<double>(const KrylovArgs &, const GmresArgs &, int, cudaStream_t);
+template cudaError_t launch_gmres<float>(const KrylovArgs &, const GmresArgs &, int, cudaStream_t);
 
 }  // namespace lgdm

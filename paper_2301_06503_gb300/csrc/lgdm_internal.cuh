@@ -112,6 +112,7 @@ struct KrylovArgs {
   int32_t max_iter;
   int32_t stall_iters;        // stop after this many iterations without a new best residual
   double rtol, newton_tol;
+  double prior_rel;           // mode 2: relative residual of the solve that produced x
   PatternView p;
   const void *vals;           // TT [nnz]
   const void *minv;           // TT [nnode*nd*nd]
@@ -127,5 +128,21 @@ template <typename TT>
 cudaError_t launch_bicgstab(const KrylovArgs &a, int nblocks, int mode, cudaStream_t s);
 template <typename TT>
 int bicgstab_max_blocks();
+
+constexpr int GMRES_MAX_M = 128;
+struct GmresArgs {
+  int32_t m;                  // restart length (<= GMRES_MAX_M)
+  int64_t ld;                 // leading dimension of the basis
+  double *V;                  // [(m+1) * ld] Krylov basis
+  double *R;                  // [m * (m+1)] rotated Hessenberg columns (block 0 writes)
+  double *y;                  // [m]
+  double *dots;               // [(GMRES_MAX_M+2) * gridDim] per-block partials
+  double *final;              // [m+2] reduced inner products
+  double *xs;                 // [ndof] scratch vector read by the SpMV
+};
+template <typename TT>
+cudaError_t launch_gmres(const KrylovArgs &a, const GmresArgs &g, int nblocks, cudaStream_t s);
+template <typename TT>
+int gmres_max_blocks();
 
 }  // namespace lgdm

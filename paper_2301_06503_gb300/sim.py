@@ -30,7 +30,7 @@ def _p(a, ct):
 
 
 def make_options(precision="fp64", precond="block", newton_tol=1e-8, krylov_rtol=None, max_newton=50,
-                 max_krylov=5000, max_halvings=6, krylov_blocks=0):
+                 max_krylov=5000, max_halvings=6, krylov_blocks=0, gmres_m=64, krylov="bicgstab"):
     o = L.Options()
     L.check(L.load().lgdm_default_options(C.byref(o)))
     o.precision = _PREC[precision]
@@ -41,6 +41,8 @@ def make_options(precision="fp64", precond="block", newton_tol=1e-8, krylov_rtol
     o.max_krylov = max_krylov
     o.max_halvings = max_halvings
     o.krylov_blocks = krylov_blocks
+    o.gmres_m = gmres_m
+    o.krylov_method = {"bicgstab": 0, "gmres": 1}[krylov]
     return o
 
 
