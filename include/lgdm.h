@@ -224,6 +224,51 @@ lgdm_status lgdm_get_counters(const lgdm_sim *sim, int64_t *counters, int32_t n)
 /* Reaction at the last committed state.  Synchronises. */
 lgdm_status lgdm_get_reaction(lgdm_sim *sim, double *reaction);
 
+/* ---------------------------------------------------------------- batches
+ * Several simulations advanced together on one stream.  Per element type,
+ * one persistent launch integrates every member's elements (tiles of a tuned
+ * block size, walked by a tuned number of resident blocks); batched launches
+ * gather the CSR values and set up the preconditioners; one cooperative
+ * launch per wave solves the members' systems, each member on its own block
+ * group and grid barrier with the group size it uses alone, so a member's
+ * results are bitwise those of the member run alone.  The launches of a
+ * Newton step up to the solve are captured once into a CUDA graph.  Members
+ * must have been created on the batch's stream with the same precision and
+ * must not be driven individually while a batch call runs.  The batch
+ * workspace (device, caller-owned, lgdm_batch_workspace_size bytes) holds
+ * the member descriptors and work lists. */
+typedef struct lgdm_batch lgdm_batch;
+lgdm_status lgdm_batch_workspace_size(int32_t n, size_t *bytes);
+lgdm_status lgdm_batch_create(lgdm_sim *const *sims, int32_t n, void *dev_workspace, size_t workspace_bytes,
+                              void *stream, lgdm_batch **out);
+void lgdm_batch_destroy(lgdm_batch *batch);
+const char *lgdm_batch_last_error(const lgdm_batch *batch);
+/* Element block size (64, 128 or 256 threads), resident blocks per SM of the
+ * persistent element launch (1..32) and CUDA-graph use.  graph_in_use: 0 no
+ * graph, 1 the assembly launches are a graph, 2 assembly and solve are.
+ * Graphs need a created stream: on the legacy default stream capture is not
+ * permitted and the launches are issued directly (lgdm_batch_last_error
+ * then holds the reason). */
+lgdm_status lgdm_batch_set_tuning(lgdm_batch *batch, int32_t block_threads, int32_t grid_factor, int32_t use_graph);
+lgdm_status lgdm_batch_get_tuning(const lgdm_batch *batch, int32_t *block_threads, int32_t *grid_factor,
+                                  int32_t *graph_in_use);
+/* Autotuner: times the batched assembly for every block size and grid factor
+ * with CUDA events on the current states and keeps the fastest. */
+lgdm_status lgdm_batch_autotune(lgdm_batch *batch, int32_t *block_threads, int32_t *grid_factor, double *ms);
+/* Batched assembly of the members with active[i] != 0 (host array of n). */
+lgdm_status lgdm_batch_assemble(lgdm_batch *batch, const int32_t *active);
+/* One Newton iteration (Algorithm 2, lines 6-18) for the active members;
+ * converged[i] = 1 converged, 0 not yet, -1 non-finite (host arrays of n,
+ * krylov_iters may be NULL).  Synchronises. */
+lgdm_status lgdm_batch_newton_step(lgdm_batch *batch, const int32_t *active, int32_t *converged,
+                                   int32_t *krylov_iters);
+/* One load step for every member to loads[i] (NaN: the member sits out):
+ * batched Newton iterations, the commit of each member at its convergence,
+ * and increment halving, member by member, for those that do not converge.
+ * newton_iters[i] and status[i] (lgdm_status of the member) may be NULL;
+ * with status NULL the first member failure is returned. */
+lgdm_status lgdm_batch_run_step(lgdm_batch *batch, const double *loads, int32_t *newton_iters, int32_t *status);
+
 /* Solve K x = b by BiCGSTAB with node-block Jacobi, allocating nothing.
  *
  * For callers that cannot allocate device memory (a host framework that has

@@ -8,11 +8,14 @@ first ``Sim`` does, and raises if the library has not been built.
 from . import _lib
 from .build import build
 
-__all__ = ["build", "Sim", "workspace_bytes", "make_options", "_lib"]
+__all__ = ["build", "Sim", "Batch", "workspace_bytes", "make_options", "_lib"]
 
 
 def __getattr__(name):
     if name in ("Sim", "workspace_bytes", "make_options"):
         from . import sim
         return getattr(sim, name)
+    if name == "Batch":
+        from . import batch
+        return batch.Batch
     raise AttributeError(name)

@@ -85,6 +85,17 @@ _SIGS = {
     "lgdm_get_timers": (C.c_int, [C.c_void_p, _dp, C.POINTER(C.c_int64)]),
     "lgdm_reset_timers": (C.c_int, [C.c_void_p]),
     "lgdm_get_counters": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.c_int32]),
+    "lgdm_batch_workspace_size": (C.c_int, [C.c_int32, C.POINTER(C.c_size_t)]),
+    "lgdm_batch_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int32, C.c_void_p, C.c_size_t, C.c_void_p,
+                                    C.POINTER(C.c_void_p)]),
+    "lgdm_batch_destroy": (None, [C.c_void_p]),
+    "lgdm_batch_last_error": (C.c_char_p, [C.c_void_p]),
+    "lgdm_batch_set_tuning": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_int32]),
+    "lgdm_batch_get_tuning": (C.c_int, [C.c_void_p, _ip, _ip, _ip]),
+    "lgdm_batch_autotune": (C.c_int, [C.c_void_p, _ip, _ip, _dp]),
+    "lgdm_batch_assemble": (C.c_int, [C.c_void_p, _ip]),
+    "lgdm_batch_newton_step": (C.c_int, [C.c_void_p, _ip, _ip, _ip]),
+    "lgdm_batch_run_step": (C.c_int, [C.c_void_p, _dp, _ip, _ip]),
     "lgdm_solve_noalloc": (C.c_int, [C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                      C.c_void_p, C.c_double, C.c_int32, C.c_void_p, _ip, _dp]),
 }

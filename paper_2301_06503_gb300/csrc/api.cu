@@ -159,6 +159,14 @@ struct lgdm_sim {
   SolveResult *res = nullptr;
   int krylov_blocks = 1;
   SolveResult last{};
+  // the simulation as a batch of one: the single path runs the batched
+  // kernels, so a member computes bitwise the same alone and in a batch
+  BatchSim *d_self = nullptr;
+  KrylovArgs *d_kself = nullptr;
+  int32_t *d_one = nullptr;            // [0] = 0 (member index), [1] = 1 (active)
+  int64_t *d_prefix = nullptr;         // tiles [0, t], gather blocks [0, g], precond blocks [0, p]
+  int32_t *d_gstart = nullptr;         // [0, krylov_blocks]
+  int64_t self_tiles = 0, self_gblocks = 0, self_pblocks = 0;
   // phase timers and counters
   bool timers_on = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -310,13 +318,19 @@ void carve(lgdm_sim &s, Carver &c) {
   s.reaction = c.take<double>(1);
   s.bar = c.take<unsigned int>(2);
   s.res = c.take<SolveResult>(1);
+  s.d_self = c.take<BatchSim>(1);
+  s.d_kself = c.take<KrylovArgs>(1);
+  s.d_one = c.take<int32_t>(2);
+  s.d_prefix = c.take<int64_t>(6);
+  s.d_gstart = c.take<int32_t>(2);
   s.ws_needed = c.off + 256;
 }
 
 int max_krylov_blocks(bool fp32) {
   static int cache[2] = {-1, -1};
   int &v = cache[fp32 ? 1 : 0];
-  if (v < 0) v = fp32 ? bicgstab_max_blocks<float>() : bicgstab_max_blocks<double>();
+  if (v < 0) v = fp32 ? std::min(bicgstab_max_blocks<float>(), bicgstab_grouped_max_blocks<float>())
+                      : std::min(bicgstab_max_blocks<double>(), bicgstab_grouped_max_blocks<double>());
   return v;
 }
 
@@ -361,6 +375,29 @@ lgdm_status plan(lgdm_sim &s, const lgdm_mesh &m, const lgdm_options &o, const l
     if (cap > 0) s.gmres_blocks = std::min(s.gmres_blocks, cap);
   }
   return LGDM_OK;
+}
+
+}  // namespace
+
+namespace {
+
+KrylovArgs krylov_args(lgdm_sim *s);
+
+BatchSim self_desc(lgdm_sim *s) {
+  BatchSim d{};
+  d.m = s->mesh_view();
+  d.mc = s->mc;
+  d.u = s->u;
+  d.kh = s->kappa_hist;
+  d.Ke = s->Ke;
+  d.re = s->re;
+  d.p = s->pattern_view();
+  d.vals = s->vals;
+  d.rraw = s->rraw;
+  d.rhs = s->rhs;
+  d.minv = s->minv;
+  d.precond = s->opt.precond;
+  return d;
 }
 
 }  // namespace
@@ -524,6 +561,27 @@ lgdm_status lgdm_create(const lgdm_mesh *m, const lgdm_material *mat, const lgdm
     e = e ? e : cudaMemsetAsync(s->u_commit, 0, sizeof(double) * s->ndof, st_);
     e = e ? e : cudaMemsetAsync(s->reaction, 0, sizeof(double), st_);
     e = e ? e : cudaMemsetAsync(s->res, 0, sizeof(SolveResult), st_);
+    BatchSim self{};
+    KrylovArgs kself{};
+    int32_t one[2] = {0, 1};
+    int64_t prefix[6] = {0, 0, 0, 0, 0, 0};
+    int32_t gstart[2] = {0, 0};
+    if (e == cudaSuccess) {
+      self = self_desc(s);
+      kself = krylov_args(s);
+      s->self_tiles = (s->nel + batch_tile_elements(s->elem, 128) - 1) / batch_tile_elements(s->elem, 128);
+      s->self_gblocks = (s->npairs + 255) / 256;
+      s->self_pblocks = (s->nnode + 127) / 128;
+      prefix[1] = s->self_tiles;
+      prefix[3] = s->self_gblocks;
+      prefix[5] = s->self_pblocks;
+      gstart[1] = s->krylov_blocks;
+      e = up(s->d_self, &self, sizeof(BatchSim));
+      e = e ? e : up(s->d_kself, &kself, sizeof(KrylovArgs));
+      e = e ? e : up(s->d_one, one, sizeof(one));
+      e = e ? e : up(s->d_prefix, prefix, sizeof(prefix));
+      e = e ? e : up(s->d_gstart, gstart, sizeof(gstart));
+    }
     e = e ? e : cudaStreamSynchronize(st_);   // host staging vectors die at return
     if (e != cudaSuccess) {
       const std::string msg = std::string("upload failed: ") + cudaGetErrorString(e);
@@ -626,37 +684,34 @@ lgdm_status lgdm_assemble(lgdm_sim *s) {
   if (!s) return fail(nullptr, LGDM_ERR_INVALID_ARG, "NULL handle");
   const MeshView mv = s->mesh_view();
   const PatternView pv = s->pattern_view();
+  const int32_t *mem = s->d_one, *act = s->d_one + 1;
+  const int64_t *tiles = s->d_prefix, *gb = s->d_prefix + 2, *pb = s->d_prefix + 4;
+  const int grid = (int)std::min<int64_t>(s->self_tiles, 2 * 152);
   if (s->opt.precision == LGDM_PREC_FP32_TANGENT) {
     {
       PhaseTimer pt(s, 0);
-      LGDM_CUDA(s, launch_element<float>(s->elem, mv, s->mc, s->u, s->kappa_hist, nullptr, s->nel,
-                                         static_cast<float *>(s->Ke), s->re, false, s->stream));
+      LGDM_CUDA(s, launch_batch_element<float>(s->elem, 128, s->d_self, mem, tiles, 1, s->self_tiles, act, grid, s->stream));
     }
     {
       PhaseTimer pt(s, 1);
-      LGDM_CUDA(s, launch_gather<float>(s->elem, pv, static_cast<float *>(s->Ke), s->re,
-                                        static_cast<float *>(s->vals), s->rraw, s->rhs, s->stream));
+      LGDM_CUDA(s, launch_batch_gather<float>(s->elem, s->d_self, mem, gb, 1, s->self_gblocks, act, s->stream));
     }
     {
       PhaseTimer pt(s, 2);
-      LGDM_CUDA(s, launch_precond<float>(s->nd, pv, static_cast<float *>(s->vals), s->opt.precond,
-                                         static_cast<float *>(s->minv), s->stream));
+      LGDM_CUDA(s, launch_batch_precond<float>(s->nd, s->d_self, mem, pb, 1, s->self_pblocks, act, s->stream));
     }
   } else {
     {
       PhaseTimer pt(s, 0);
-      LGDM_CUDA(s, launch_element<double>(s->elem, mv, s->mc, s->u, s->kappa_hist, nullptr, s->nel,
-                                          static_cast<double *>(s->Ke), s->re, false, s->stream));
+      LGDM_CUDA(s, launch_batch_element<double>(s->elem, 128, s->d_self, mem, tiles, 1, s->self_tiles, act, grid, s->stream));
     }
     {
       PhaseTimer pt(s, 1);
-      LGDM_CUDA(s, launch_gather<double>(s->elem, pv, static_cast<double *>(s->Ke), s->re,
-                                         static_cast<double *>(s->vals), s->rraw, s->rhs, s->stream));
+      LGDM_CUDA(s, launch_batch_gather<double>(s->elem, s->d_self, mem, gb, 1, s->self_gblocks, act, s->stream));
     }
     {
       PhaseTimer pt(s, 2);
-      LGDM_CUDA(s, launch_precond<double>(s->nd, pv, static_cast<double *>(s->vals), s->opt.precond,
-                                          static_cast<double *>(s->minv), s->stream));
+      LGDM_CUDA(s, launch_batch_precond<double>(s->nd, s->d_self, mem, pb, 1, s->self_pblocks, act, s->stream));
     }
   }
   s->counters[0] += 3;
@@ -726,7 +781,6 @@ KrylovArgs krylov_args(lgdm_sim *s) {
   a.ph = s->kv[7];
   a.sh = s->kv[8];
   a.xb = s->kv[9];
-  a.prior_rel = s->last.rel_res;
   a.stall_iters = std::max(500, s->opt.max_krylov / 4);
   a.u = s->u;
   a.partial = s->partial;
@@ -755,12 +809,15 @@ lgdm_status finish_launch(lgdm_sim *s, int mode, SolveResult *out) {
 
 lgdm_status run_krylov(lgdm_sim *s, int mode, SolveResult *out) {
   const KrylovArgs a = krylov_args(s);
+  (void)a;
   {
     PhaseTimer pt(s, 3);
     if (s->opt.precision == LGDM_PREC_FP32_TANGENT)
-      LGDM_CUDA(s, launch_bicgstab<float>(a, s->krylov_blocks, mode, s->stream));
+      LGDM_CUDA(s, launch_bicgstab_grouped<float>(s->nd, s->d_kself, s->d_one, s->d_gstart, s->d_one + 1, 1,
+                                                  s->krylov_blocks, mode, s->stream));
     else
-      LGDM_CUDA(s, launch_bicgstab<double>(a, s->krylov_blocks, mode, s->stream));
+      LGDM_CUDA(s, launch_bicgstab_grouped<double>(s->nd, s->d_kself, s->d_one, s->d_gstart, s->d_one + 1, 1,
+                                                   s->krylov_blocks, mode, s->stream));
   }
   return finish_launch(s, mode, out);
 }
@@ -976,3 +1033,507 @@ extern "C" lgdm_status lgdm_run_step(lgdm_sim *s, double load, int32_t *newton_i
   if (newton_iters) *newton_iters = its;
   return st;
 }
+
+// ====================================================================== batch
+// Several simulations advanced together: one persistent element launch per
+// element type over all members' tiles, batched gather and preconditioner
+// set-up, one cooperative BiCGSTAB launch per wave of members (each member on
+// its own block group and barrier, with the group size it uses alone), the
+// batched update, and a CUDA graph of the launches of a Newton step.
+struct lgdm_batch {
+  std::vector<lgdm_sim *> sims;
+  int n = 0;
+  cudaStream_t stream = nullptr;
+  bool fp32 = false;
+  char *ws = nullptr;
+  size_t ws_bytes = 0;
+  BatchSim *d_sims = nullptr;
+  KrylovArgs *d_kargs = nullptr;
+  int32_t *d_active = nullptr;
+  SolveResult *d_res = nullptr;
+  struct Group {                       // members of one element type
+    int elem = 0, nd = 0;
+    std::vector<int32_t> members;
+    int32_t *d_members = nullptr;
+    int64_t *d_tile = nullptr, *d_gblock = nullptr, *d_pblock = nullptr;
+    int64_t tiles = 0, gblocks = 0, pblocks = 0;
+  };
+  std::vector<Group> groups;
+  struct Wave {                        // members whose block groups fit one co-resident launch
+    int nd = 0;
+    std::vector<int32_t> members;
+    int32_t *d_members = nullptr, *d_start = nullptr;
+    int blocks = 0;
+  };
+  std::vector<Wave> waves;
+  int bt = 128, grid_factor = 2, sms = 152;
+  bool graph_on = true, graph_ok = false, graph_tried = false;
+  int graph_mode = 0;                  // 0 none, 1 assembly launches, 2 assembly and solve
+  int direct_issues = 0;
+  std::string graph_note;
+  cudaGraphExec_t graph = nullptr;
+  std::vector<int32_t> h_active;
+  std::vector<SolveResult> h_res;
+  std::string err;
+  ~lgdm_batch() {
+    if (graph) cudaGraphExecDestroy(graph);
+  }
+};
+
+namespace {
+
+size_t batch_bytes(int n) {
+  // descriptors, flags, results and prefix arrays; a generous bound per member
+  return (size_t)n * (sizeof(BatchSim) + sizeof(KrylovArgs) + sizeof(SolveResult) + 4 * 64 + 10 * 8) +
+         (size_t)(n + 8) * 8 * 24 + (1 << 16);
+}
+
+lgdm_status bfail(lgdm_batch *b, lgdm_status st, const std::string &m) {
+  if (b) b->err = m;
+  g_last_error = m;
+  return st;
+}
+
+#define LGDM_BCUDA(b, call)                                                                          \
+  do {                                                                                               \
+    cudaError_t _e = (call);                                                                         \
+    if (_e != cudaSuccess) return bfail(b, LGDM_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(_e)); \
+  } while (0)
+
+// The launches of one batched Newton step up to the solve (mode 0).
+lgdm_status batch_issue_assembly(lgdm_batch *b) {
+  const int grid_cap = b->grid_factor * b->sms;
+  for (auto &g : b->groups) {
+    const int grid = (int)std::min<int64_t>(g.tiles, grid_cap);
+    if (b->fp32) {
+      LGDM_BCUDA(b, launch_batch_element<float>(g.elem, b->bt, b->d_sims, g.d_members, g.d_tile, (int)g.members.size(),
+                                                g.tiles, b->d_active, grid, b->stream));
+      LGDM_BCUDA(b, launch_batch_gather<float>(g.elem, b->d_sims, g.d_members, g.d_gblock, (int)g.members.size(),
+                                               g.gblocks, b->d_active, b->stream));
+      LGDM_BCUDA(b, launch_batch_precond<float>(g.nd, b->d_sims, g.d_members, g.d_pblock, (int)g.members.size(),
+                                                g.pblocks, b->d_active, b->stream));
+    } else {
+      LGDM_BCUDA(b, launch_batch_element<double>(g.elem, b->bt, b->d_sims, g.d_members, g.d_tile, (int)g.members.size(),
+                                                 g.tiles, b->d_active, grid, b->stream));
+      LGDM_BCUDA(b, launch_batch_gather<double>(g.elem, b->d_sims, g.d_members, g.d_gblock, (int)g.members.size(),
+                                                g.gblocks, b->d_active, b->stream));
+      LGDM_BCUDA(b, launch_batch_precond<double>(g.nd, b->d_sims, g.d_members, g.d_pblock, (int)g.members.size(),
+                                                 g.pblocks, b->d_active, b->stream));
+    }
+  }
+  return LGDM_OK;
+}
+
+lgdm_status batch_issue_solve(lgdm_batch *b, int mode) {
+  for (auto &w : b->waves) {
+    if (b->fp32)
+      LGDM_BCUDA(b, launch_bicgstab_grouped<float>(w.nd, b->d_kargs, w.d_members, w.d_start, b->d_active,
+                                                   (int)w.members.size(), w.blocks, mode, b->stream));
+    else
+      LGDM_BCUDA(b, launch_bicgstab_grouped<double>(w.nd, b->d_kargs, w.d_members, w.d_start, b->d_active,
+                                                    (int)w.members.size(), w.blocks, mode, b->stream));
+  }
+  return LGDM_OK;
+}
+
+// Capture the given launches into an executable graph; false if refused.
+bool batch_capture(lgdm_batch *b, bool with_solve) {
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) {
+    b->graph_note = std::string("begin capture: ") + cudaGetErrorString(e);
+    cudaGetLastError();
+    return false;
+  }
+  lgdm_status st = batch_issue_assembly(b);
+  if (st == LGDM_OK && with_solve) st = batch_issue_solve(b, 0);
+  e = cudaStreamEndCapture(b->stream, &g);
+  bool ok = false;
+  if (st == LGDM_OK && e == cudaSuccess && g) {
+    e = cudaGraphInstantiate(&b->graph, g, 0);
+    ok = e == cudaSuccess;
+  }
+  if (!ok) b->graph_note = (st != LGDM_OK) ? b->err : std::string(cudaGetErrorString(e));
+  if (g) cudaGraphDestroy(g);
+  cudaGetLastError();
+  return ok;
+}
+
+lgdm_status batch_assemble_and_solve(lgdm_batch *b) {
+  // the first step runs directly (kernel attributes get set outside any capture)
+  if (b->graph_on && !b->graph_tried && b->direct_issues > 0) {
+    b->graph_tried = true;
+    if (batch_capture(b, true)) b->graph_mode = 2;
+    else if (batch_capture(b, false)) b->graph_mode = 1;
+    b->graph_ok = b->graph_mode > 0;
+  }
+  if (b->graph_on && b->graph_ok) {
+    LGDM_BCUDA(b, cudaGraphLaunch(b->graph, b->stream));
+    if (b->graph_mode == 1) return batch_issue_solve(b, 0);
+    return LGDM_OK;
+  }
+  ++b->direct_issues;
+  lgdm_status st = batch_issue_assembly(b);
+  if (st != LGDM_OK) return st;
+  return batch_issue_solve(b, 0);
+}
+
+}  // namespace
+
+extern "C" {
+
+lgdm_status lgdm_batch_workspace_size(int32_t n, size_t *bytes) {
+  if (n <= 0 || !bytes) return fail(nullptr, LGDM_ERR_INVALID_ARG, "bad batch size");
+  *bytes = batch_bytes(n);
+  return LGDM_OK;
+}
+
+lgdm_status lgdm_batch_create(lgdm_sim *const *sims, int32_t n, void *ws, size_t ws_bytes, void *stream,
+                              lgdm_batch **out) {
+  if (!sims || n <= 0 || !out || !ws) return fail(nullptr, LGDM_ERR_INVALID_ARG, "bad batch arguments");
+  *out = nullptr;
+  if (ws_bytes < batch_bytes(n)) return fail(nullptr, LGDM_ERR_OOM, "batch workspace too small");
+  lgdm_batch *b = nullptr;
+  try {
+    b = new lgdm_batch();
+    b->n = n;
+    b->stream = static_cast<cudaStream_t>(stream);
+    b->ws = static_cast<char *>(ws);
+    b->ws_bytes = ws_bytes;
+    for (int i = 0; i < n; ++i) {
+      lgdm_sim *s = sims[i];
+      if (!s) { delete b; return fail(nullptr, LGDM_ERR_INVALID_ARG, "NULL member"); }
+      if (s->stream != b->stream) { delete b; return fail(nullptr, LGDM_ERR_INVALID_ARG, "members must use the batch stream"); }
+      const bool f = s->opt.precision == LGDM_PREC_FP32_TANGENT;
+      if (i == 0) b->fp32 = f;
+      else if (f != b->fp32) { delete b; return fail(nullptr, LGDM_ERR_INVALID_ARG, "members must share the precision"); }
+      b->sims.push_back(s);
+    }
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev);
+    Carver c{b->ws};
+    b->d_sims = c.take<BatchSim>(n);
+    b->d_kargs = c.take<KrylovArgs>(n);
+    b->d_active = c.take<int32_t>(n);
+    b->d_res = c.take<SolveResult>(n);
+    std::vector<BatchSim> hs(n);
+    std::vector<KrylovArgs> hk(n);
+    for (int i = 0; i < n; ++i) {
+      lgdm_sim *s = b->sims[i];
+      BatchSim &d = hs[i];
+      d.m = s->mesh_view();
+      d.mc = s->mc;
+      d.u = s->u;
+      d.kh = s->kappa_hist;
+      d.Ke = s->Ke;
+      d.re = s->re;
+      d.p = s->pattern_view();
+      d.vals = s->vals;
+      d.rraw = s->rraw;
+      d.rhs = s->rhs;
+      d.minv = s->minv;
+      d.precond = s->opt.precond;
+      hk[i] = krylov_args(s);
+    }
+    // element-type groups
+    for (int elem : {LGDM_L2, LGDM_Q4, LGDM_H8}) {
+      lgdm_batch::Group g;
+      g.elem = elem;
+      g.nd = dim_of(elem) + 1;
+      for (int i = 0; i < n; ++i)
+        if (b->sims[i]->elem == elem) g.members.push_back(i);
+      if (!g.members.empty()) b->groups.push_back(g);
+    }
+    const int epb = 1;   // prefixes are in tiles of the tuned block size: rebuilt by set_tiles
+    (void)epb;
+    const size_t nm_max = n;
+    for (auto &g : b->groups) {
+      const int m = (int)g.members.size();
+      g.d_members = c.take<int32_t>(nm_max);
+      g.d_tile = c.take<int64_t>(m + 1);
+      g.d_gblock = c.take<int64_t>(m + 1);
+      g.d_pblock = c.take<int64_t>(m + 1);
+      std::vector<int64_t> gb(m + 1, 0), pbk(m + 1, 0);
+      for (int j = 0; j < m; ++j) {
+        lgdm_sim *s = b->sims[g.members[j]];
+        gb[j + 1] = gb[j] + (s->npairs + 255) / 256;
+        pbk[j + 1] = pbk[j] + (s->nnode + 127) / 128;
+      }
+      g.gblocks = gb[m];
+      g.pblocks = pbk[m];
+      LGDM_BCUDA(b, cudaMemcpyAsync(g.d_members, g.members.data(), sizeof(int32_t) * m, cudaMemcpyHostToDevice, b->stream));
+      LGDM_BCUDA(b, cudaMemcpyAsync(g.d_gblock, gb.data(), sizeof(int64_t) * (m + 1), cudaMemcpyHostToDevice, b->stream));
+      LGDM_BCUDA(b, cudaMemcpyAsync(g.d_pblock, pbk.data(), sizeof(int64_t) * (m + 1), cudaMemcpyHostToDevice, b->stream));
+    }
+    // waves: members with the same nd, each with the block group it uses alone
+    const int cap = b->fp32 ? bicgstab_grouped_max_blocks<float>() : bicgstab_grouped_max_blocks<double>();
+    for (int nd = 2; nd <= 4; ++nd) {
+      lgdm_batch::Wave w;
+      w.nd = nd;
+      for (int i = 0; i < n; ++i) {
+        lgdm_sim *s = b->sims[i];
+        if (s->nd != nd) continue;
+        if (s->krylov_blocks > cap) { delete b; return fail(nullptr, LGDM_ERR_INVALID_ARG, "member Krylov grid too large"); }
+        if (w.blocks + s->krylov_blocks > cap) {
+          b->waves.push_back(w);
+          w = lgdm_batch::Wave();
+          w.nd = nd;
+        }
+        w.members.push_back(i);
+        w.blocks += s->krylov_blocks;
+      }
+      if (!w.members.empty()) b->waves.push_back(w);
+    }
+    for (auto &w : b->waves) {
+      const int m = (int)w.members.size();
+      std::vector<int32_t> st(m + 1, 0);
+      for (int j = 0; j < m; ++j) st[j + 1] = st[j] + b->sims[w.members[j]]->krylov_blocks;
+      w.d_members = c.take<int32_t>(m);
+      w.d_start = c.take<int32_t>(m + 1);
+      LGDM_BCUDA(b, cudaMemcpyAsync(w.d_members, w.members.data(), sizeof(int32_t) * m, cudaMemcpyHostToDevice, b->stream));
+      LGDM_BCUDA(b, cudaMemcpyAsync(w.d_start, st.data(), sizeof(int32_t) * (m + 1), cudaMemcpyHostToDevice, b->stream));
+    }
+    if (c.off > ws_bytes) { delete b; return fail(nullptr, LGDM_ERR_OOM, "batch workspace too small"); }
+    LGDM_BCUDA(b, cudaMemcpyAsync(b->d_sims, hs.data(), sizeof(BatchSim) * n, cudaMemcpyHostToDevice, b->stream));
+    LGDM_BCUDA(b, cudaMemcpyAsync(b->d_kargs, hk.data(), sizeof(KrylovArgs) * n, cudaMemcpyHostToDevice, b->stream));
+    b->h_active.assign(n, 0);
+    b->h_res.resize(n);
+    // tile prefixes for the default block size
+    for (auto &g : b->groups) {
+      const int m = (int)g.members.size();
+      std::vector<int64_t> tl(m + 1, 0);
+      const int epb_ = batch_tile_elements(g.elem, b->bt);
+      for (int j = 0; j < m; ++j) tl[j + 1] = tl[j] + (b->sims[g.members[j]]->nel + epb_ - 1) / epb_;
+      g.tiles = tl[m];
+      LGDM_BCUDA(b, cudaMemcpyAsync(g.d_tile, tl.data(), sizeof(int64_t) * (m + 1), cudaMemcpyHostToDevice, b->stream));
+    }
+    LGDM_BCUDA(b, cudaStreamSynchronize(b->stream));
+    *out = b;
+    return LGDM_OK;
+  } catch (...) {
+    delete b;
+    return fail(nullptr, LGDM_ERR_INVALID_ARG, "host exception while creating the batch");
+  }
+}
+
+void lgdm_batch_destroy(lgdm_batch *b) { delete b; }
+
+const char *lgdm_batch_last_error(const lgdm_batch *b) { return b ? b->err.c_str() : g_last_error.c_str(); }
+
+lgdm_status lgdm_batch_set_tuning(lgdm_batch *b, int32_t block_threads, int32_t grid_factor, int32_t use_graph) {
+  if (!b || (block_threads != 64 && block_threads != 128 && block_threads != 256) || grid_factor < 1 || grid_factor > 32)
+    return bfail(b, LGDM_ERR_INVALID_ARG, "block_threads must be 64, 128 or 256; grid_factor 1..32");
+  b->bt = block_threads;
+  b->grid_factor = grid_factor;
+  b->graph_on = use_graph != 0;
+  if (b->graph) cudaGraphExecDestroy(b->graph);
+  b->graph = nullptr;
+  b->graph_ok = b->graph_tried = false;
+  b->graph_mode = 0;
+  b->direct_issues = 0;
+  for (auto &g : b->groups) {
+    const int m = (int)g.members.size();
+    std::vector<int64_t> tl(m + 1, 0);
+    const int epb = batch_tile_elements(g.elem, b->bt);
+    for (int j = 0; j < m; ++j) tl[j + 1] = tl[j] + (b->sims[g.members[j]]->nel + epb - 1) / epb;
+    g.tiles = tl[m];
+    LGDM_BCUDA(b, cudaMemcpyAsync(g.d_tile, tl.data(), sizeof(int64_t) * (m + 1), cudaMemcpyHostToDevice, b->stream));
+  }
+  LGDM_BCUDA(b, cudaStreamSynchronize(b->stream));
+  return LGDM_OK;
+}
+
+lgdm_status lgdm_batch_get_tuning(const lgdm_batch *b, int32_t *block_threads, int32_t *grid_factor, int32_t *graph) {
+  if (!b) return fail(nullptr, LGDM_ERR_INVALID_ARG, "NULL batch");
+  if (block_threads) *block_threads = b->bt;
+  if (grid_factor) *grid_factor = b->grid_factor;
+  if (graph) *graph = (b->graph_on && b->graph_ok) ? b->graph_mode : 0;
+  if (b->graph_tried && !b->graph_ok) const_cast<lgdm_batch *>(b)->err = "graph capture refused: " + b->graph_note;
+  return LGDM_OK;
+}
+
+lgdm_status lgdm_batch_newton_step(lgdm_batch *b, const int32_t *active, int32_t *converged, int32_t *krylov_iters) {
+  if (!b || !active) return bfail(b, LGDM_ERR_INVALID_ARG, "NULL argument");
+  int nact = 0;
+  for (int i = 0; i < b->n; ++i) {
+    b->h_active[i] = active[i] ? 1 : 0;
+    nact += b->h_active[i];
+  }
+  if (nact == 0) return LGDM_OK;
+  LGDM_BCUDA(b, cudaMemcpyAsync(b->d_active, b->h_active.data(), sizeof(int32_t) * b->n, cudaMemcpyHostToDevice, b->stream));
+  lgdm_status st = batch_assemble_and_solve(b);
+  if (st != LGDM_OK) return st;
+  LGDM_BCUDA(b, launch_collect_results(b->d_kargs, b->n, b->d_res, b->stream));
+  LGDM_BCUDA(b, cudaMemcpyAsync(b->h_res.data(), b->d_res, sizeof(SolveResult) * b->n, cudaMemcpyDeviceToHost, b->stream));
+  LGDM_BCUDA(b, cudaStreamSynchronize(b->stream));
+  // members the first solve left far from its tolerance: GMRES, one by one
+  for (int i = 0; i < b->n; ++i) {
+    if (!b->h_active[i]) continue;
+    lgdm_sim *s = b->sims[i];
+    SolveResult &r = b->h_res[i];
+    s->counters[0] += 4;
+    s->counters[1] += 1;
+    s->counters[2] += r.iters;
+    s->last = r;
+    if (r.status == 4) return bfail(b, LGDM_ERR_TIMEOUT, "grid barrier timed out in a grouped Krylov launch");
+    const bool nonfinite = r.status == 3;
+    if ((nonfinite || (r.status != 0 && r.rel_res > 1e3 * s->opt.krylov_rtol)) && s->opt.gmres_m > 0) {
+      if (nonfinite)
+        LGDM_BCUDA(b, cudaMemsetAsync(s->kv[0], 0, sizeof(double) * s->ndof, s->stream));
+      else
+        LGDM_BCUDA(b, cudaMemcpyAsync(s->kv[0], s->kv[9], sizeof(double) * s->ndof, cudaMemcpyDeviceToDevice, s->stream));
+      SolveResult g{};
+      const int32_t bi = r.iters;
+      st = run_gmres(s, &g);
+      if (st != LGDM_OK && st != LGDM_ERR_NONFINITE) return bfail(b, st, s->err);
+      g.iters += bi;
+      s->last.iters = g.iters;
+      r = g;
+    }
+    if (krylov_iters) krylov_iters[i] = r.iters;
+  }
+  // batched update and Newton test (mode 2), same block groups
+  st = batch_issue_solve(b, 2);
+  if (st != LGDM_OK) return st;
+  LGDM_BCUDA(b, launch_collect_results(b->d_kargs, b->n, b->d_res, b->stream));
+  LGDM_BCUDA(b, cudaMemcpyAsync(b->h_res.data(), b->d_res, sizeof(SolveResult) * b->n, cudaMemcpyDeviceToHost, b->stream));
+  LGDM_BCUDA(b, cudaStreamSynchronize(b->stream));
+  for (int i = 0; i < b->n; ++i) {
+    if (!b->h_active[i]) continue;
+    lgdm_sim *s = b->sims[i];
+    const SolveResult &r = b->h_res[i];
+    s->counters[0] += 1;
+    s->last.converged = r.converged;
+    for (int k = 0; k < 4; ++k) s->last.norms[k] = r.norms[k];
+    s->assembled = false;
+    if (r.status == 4) return bfail(b, LGDM_ERR_TIMEOUT, "grid barrier timed out in the batched update");
+    if (converged) converged[i] = (r.status == 3) ? -1 : r.converged;
+  }
+  return LGDM_OK;
+}
+
+lgdm_status lgdm_batch_run_step(lgdm_batch *b, const double *loads, int32_t *newton_iters, int32_t *status) {
+  if (!b || !loads) return bfail(b, LGDM_ERR_INVALID_ARG, "NULL argument");
+  const int n = b->n;
+  std::vector<int32_t> act(n, 0), conv(n, 0), its(n, 0);
+  int max_newton = 0;
+  for (int i = 0; i < n; ++i) {
+    if (newton_iters) newton_iters[i] = 0;
+    if (status) status[i] = LGDM_OK;
+    if (loads[i] != loads[i]) continue;          // NaN: member sits this step out
+    lgdm_status st = lgdm_begin_step(b->sims[i], loads[i]);
+    if (st != LGDM_OK) return bfail(b, st, b->sims[i]->err);
+    act[i] = 1;
+    max_newton = std::max(max_newton, b->sims[i]->opt.max_newton);
+  }
+  std::vector<int32_t> todo(act);
+  for (int k = 1; k <= max_newton; ++k) {
+    bool any = false;
+    for (int i = 0; i < n; ++i)
+      if (act[i] && k > b->sims[i]->opt.max_newton) act[i] = 0;
+    for (int i = 0; i < n; ++i) any = any || act[i];
+    if (!any) break;
+    lgdm_status st = lgdm_batch_newton_step(b, act.data(), conv.data(), nullptr);
+    if (st != LGDM_OK) return st;
+    for (int i = 0; i < n; ++i) {
+      if (!act[i]) continue;
+      its[i] = k;
+      b->sims[i]->counters[3] += 1;
+      if (conv[i] == 1) {
+        st = lgdm_commit(b->sims[i]);
+        if (st != LGDM_OK) return bfail(b, st, b->sims[i]->err);
+        b->sims[i]->load_commit = loads[i];
+        act[i] = 0;
+        todo[i] = 0;
+      } else if (conv[i] == -1) {
+        act[i] = 0;                                // diverged: halve below
+      }
+    }
+  }
+  // members that did not converge: increment halving from the committed state, alone
+  for (int i = 0; i < n; ++i) {
+    if (!todo[i]) continue;
+    lgdm_sim *s = b->sims[i];
+    LGDM_BCUDA(b, cudaMemcpyAsync(s->u, s->u_commit, sizeof(double) * s->ndof, cudaMemcpyDeviceToDevice, s->stream));
+    int32_t extra = 0;
+    lgdm_status st = LGDM_ERR_NOT_CONVERGED;
+    if (s->opt.max_halvings > 0) {
+      const double from = s->load_commit, mid = 0.5 * (from + loads[i]);
+      s->counters[5] += 1;
+      st = advance(s, from, mid, 1, &extra);
+      if (st == LGDM_OK) st = advance(s, mid, loads[i], 1, &extra);
+    }
+    its[i] += extra;
+    if (status) status[i] = st;
+    else if (st != LGDM_OK) return bfail(b, st, s->err);
+  }
+  if (newton_iters)
+    for (int i = 0; i < n; ++i) newton_iters[i] = its[i];
+  return LGDM_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+lgdm_status batch_assemble_only(lgdm_batch *b) { return batch_issue_assembly(b); }
+
+}  // namespace
+
+extern "C" {
+
+lgdm_status lgdm_batch_assemble(lgdm_batch *b, const int32_t *active) {
+  if (!b || !active) return bfail(b, LGDM_ERR_INVALID_ARG, "NULL argument");
+  for (int i = 0; i < b->n; ++i) b->h_active[i] = active[i] ? 1 : 0;
+  LGDM_BCUDA(b, cudaMemcpyAsync(b->d_active, b->h_active.data(), sizeof(int32_t) * b->n, cudaMemcpyHostToDevice, b->stream));
+  lgdm_status st = batch_assemble_only(b);
+  for (int i = 0; i < b->n; ++i)
+    if (b->h_active[i]) {
+      b->sims[i]->assembled = true;
+      b->sims[i]->counters[0] += 3;
+      b->sims[i]->counters[1] += 1;
+    }
+  return st;
+}
+
+lgdm_status lgdm_batch_autotune(lgdm_batch *b, int32_t *block_threads, int32_t *grid_factor, double *best_ms) {
+  if (!b) return fail(nullptr, LGDM_ERR_INVALID_ARG, "NULL batch");
+  std::vector<int32_t> all(b->n, 1);
+  cudaEvent_t e0, e1;
+  LGDM_BCUDA(b, cudaEventCreate(&e0));
+  LGDM_BCUDA(b, cudaEventCreate(&e1));
+  double best = 1e300;
+  int bbt = b->bt, bgf = b->grid_factor;
+  const bool g = b->graph_on;
+  for (int bt : {64, 128, 256})
+    for (int gf : {1, 2, 4, 8}) {
+      lgdm_status st = lgdm_batch_set_tuning(b, bt, gf, g);
+      if (st != LGDM_OK) return st;
+      st = lgdm_batch_assemble(b, all.data());            // warm-up (and attribute set-up)
+      if (st != LGDM_OK) return st;
+      LGDM_BCUDA(b, cudaEventRecord(e0, b->stream));
+      for (int r = 0; r < 3; ++r) {
+        st = batch_assemble_only(b);
+        if (st != LGDM_OK) return st;
+      }
+      LGDM_BCUDA(b, cudaEventRecord(e1, b->stream));
+      LGDM_BCUDA(b, cudaEventSynchronize(e1));
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms / 3.0 < best) {
+        best = ms / 3.0;
+        bbt = bt;
+        bgf = gf;
+      }
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  lgdm_status st = lgdm_batch_set_tuning(b, bbt, bgf, g);
+  if (block_threads) *block_threads = bbt;
+  if (grid_factor) *grid_factor = bgf;
+  if (best_ms) *best_ms = best;
+  return st;
+}
+
+}  // extern "C"

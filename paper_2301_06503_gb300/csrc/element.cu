@@ -127,10 +127,10 @@ __device__ __forceinline__ double equivalent_strain(const MatConst &mc, const do
 // ------------------------------------------------------------------ element kernel
 constexpr int ELEM_THREADS = 128;
 
-template <int ELEM, typename TT>
+template <int ELEM, typename TT, int BT = ELEM_THREADS>
 struct ElemLayout {
   static constexpr int DIM = Elem<ELEM>::DIM, NEN = Elem<ELEM>::NEN, NV = Elem<ELEM>::NV;
-  static constexpr int ND = DIM + 1, NGP = NEN, EPB = ELEM_THREADS / NEN;
+  static constexpr int ND = DIM + 1, NGP = NEN, EPB = BT / NEN;
   // double record per Gauss point: dNdx[NEN][DIM], sig dV[NV], rho2, rho4, gbar[DIM]
   static constexpr int RD = NEN * DIM + NV + 2 + DIM;
   static constexpr int O_DN = 0, O_SIG = NEN * DIM, O_R2 = O_SIG + NV, O_R4 = O_R2 + 1, O_GB = O_R4 + 1;
@@ -147,12 +147,14 @@ struct ElemLayout {
   }
 };
 
-template <int ELEM, typename TT, bool RES_ONLY>
-__global__ void __launch_bounds__(ELEM_THREADS)
-element_kernel(MeshView m, MatConst mc, const double *__restrict__ u, const double *__restrict__ kh,
-               const int32_t *__restrict__ elem_list, int32_t n_elem, TT *__restrict__ Ke,
-               double *__restrict__ re) {
-  using L = ElemLayout<ELEM, TT>;
+// One tile of EPB elements: phase 1 and phase 2 for tile `tile` of an
+// element list.  Every thread of the block calls it (it synchronises).
+template <int ELEM, typename TT, bool RES_ONLY, int BT = ELEM_THREADS>
+__device__ __forceinline__ void element_tile(const MeshView &m, const MatConst &mc, const double *__restrict__ u,
+                                             const double *__restrict__ kh, const int32_t *__restrict__ elem_list,
+                                             int32_t n_elem, TT *__restrict__ Ke, double *__restrict__ re,
+                                             int64_t tile) {
+  using L = ElemLayout<ELEM, TT, BT>;
   constexpr int DIM = L::DIM, NEN = L::NEN, NV = L::NV, ND = L::ND, NGP = L::NGP, EPB = L::EPB;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double *sN = reinterpret_cast<double *>(smem_raw);            // [NGP][NEN]
@@ -164,12 +166,12 @@ element_kernel(MeshView m, MatConst mc, const double *__restrict__ u, const doub
 
   const int tid = threadIdx.x;
   const int el = tid / NEN, a = tid % NEN;
-  const int64_t slot = (int64_t)blockIdx.x * EPB + el;           // position in the element list
+  const int64_t slot = tile * EPB + el;                          // position in the element list
   const bool valid = slot < n_elem;
   const int32_t e = valid ? (elem_list ? elem_list[slot] : (int32_t)slot) : 0;
 
-  for (int k = tid; k < NGP * NEN; k += ELEM_THREADS) sN[k] = shape_N<DIM>(k / NEN, k % NEN);
-  for (int k = tid; k < NGP * NEN * DIM; k += ELEM_THREADS)
+  for (int k = tid; k < NGP * NEN; k += BT) sN[k] = shape_N<DIM>(k / NEN, k % NEN);
+  for (int k = tid; k < NGP * NEN * DIM; k += BT)
     sdN[k] = shape_dN<DIM>(k / (NEN * DIM), (k / DIM) % NEN, k % DIM);
   if (valid) {
     const int32_t node = m.conn[(int64_t)e * NEN + a];
@@ -322,7 +324,7 @@ element_kernel(MeshView m, MatConst mc, const double *__restrict__ u, const doub
     }
   }
   __syncthreads();
-  if (!valid) return;
+  if (!valid) return;                                            // no barrier follows in this tile
 
   // ---------------- phase 2: block row a
   const double *RD0 = recD + el * L::RDS;
@@ -430,6 +432,14 @@ element_kernel(MeshView m, MatConst mc, const double *__restrict__ u, const doub
 }
 
 template <int ELEM, typename TT, bool RES_ONLY>
+__global__ void __launch_bounds__(ELEM_THREADS)
+element_kernel(MeshView m, MatConst mc, const double *__restrict__ u, const double *__restrict__ kh,
+               const int32_t *__restrict__ elem_list, int32_t n_elem, TT *__restrict__ Ke,
+               double *__restrict__ re) {
+  element_tile<ELEM, TT, RES_ONLY>(m, mc, u, kh, elem_list, n_elem, Ke, re, blockIdx.x);
+}
+
+template <int ELEM, typename TT, bool RES_ONLY>
 static cudaError_t launch_element_t(const MeshView &m, const MatConst &mc, const double *u,
                                     const double *kh, const int32_t *list, int32_t n, TT *Ke, double *re,
                                     cudaStream_t s) {
@@ -468,10 +478,9 @@ template cudaError_t launch_element<float>(int, const MeshView &, const MatConst
 
 // ------------------------------------------------------------------ gather
 template <int ND, int NEN, typename TT>
-__global__ void __launch_bounds__(256)
-gather_kernel(PatternView p, const TT *__restrict__ Ke, const double *__restrict__ re,
-              TT *__restrict__ vals, double *__restrict__ rraw, double *__restrict__ rhs) {
-  const int64_t pr = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void gather_pair(const PatternView &p, const TT *__restrict__ Ke,
+                                            const double *__restrict__ re, TT *__restrict__ vals,
+                                            double *__restrict__ rraw, double *__restrict__ rhs, int64_t pr) {
   if (pr >= p.npairs) return;
   const int32_t a = p.pair_node[pr], b = p.nbr[pr];
   const int32_t pb = p.nbr_ptr[a];
@@ -521,6 +530,13 @@ gather_kernel(PatternView p, const TT *__restrict__ Ke, const double *__restrict
   }
 }
 
+template <int ND, int NEN, typename TT>
+__global__ void __launch_bounds__(256)
+gather_kernel(PatternView p, const TT *__restrict__ Ke, const double *__restrict__ re,
+              TT *__restrict__ vals, double *__restrict__ rraw, double *__restrict__ rhs) {
+  gather_pair<ND, NEN, TT>(p, Ke, re, vals, rraw, rhs, (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
+}
+
 template <typename TT>
 cudaError_t launch_gather(int elem, const PatternView &p, const TT *Ke, const double *re, TT *vals,
                           double *rraw, double *rhs, cudaStream_t s) {
@@ -542,8 +558,8 @@ template cudaError_t launch_gather<float>(int, const PatternView &, const float 
 // Inverse of each node's nd x nd diagonal block (Gauss-Jordan, partial
 // pivoting, in double), or of its diagonal only (point Jacobi).
 template <int ND, typename TT>
-__global__ void precond_kernel(PatternView p, const TT *__restrict__ vals, int kind, TT *__restrict__ minv) {
-  const int32_t a = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void precond_node(const PatternView &p, const TT *__restrict__ vals, int kind,
+                                             TT *__restrict__ minv, int32_t a) {
   if (a >= p.nnode) return;
   const int32_t pb = p.nbr_ptr[a], deg = p.nbr_ptr[a + 1] - pb;
   const int32_t s = p.diag_pair[a] - pb;
@@ -585,6 +601,11 @@ __global__ void precond_kernel(PatternView p, const TT *__restrict__ vals, int k
   for (int i = 0; i < ND; ++i)
 #pragma unroll
     for (int j = 0; j < ND; ++j) minv[((int64_t)a * ND + i) * ND + j] = (TT)M[i][ND + j];
+}
+
+template <int ND, typename TT>
+__global__ void precond_kernel(PatternView p, const TT *__restrict__ vals, int kind, TT *__restrict__ minv) {
+  precond_node<ND, TT>(p, vals, kind, minv, blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 template <typename TT>
@@ -694,5 +715,133 @@ cudaError_t launch_reaction_sum(const double *re, const int32_t *idx, const doub
   reaction_sum_kernel<<<1, 256, 0, s>>>(re, idx, w, n, out);
   return cudaGetLastError();
 }
+
+// ------------------------------------------------------------------ batched kernels
+// Many simulations of one element type in one launch.  The members' element
+// tiles (pairs, nodes) are numbered consecutively; a block finds its member
+// by binary search in the prefix array.  Inactive members are skipped.
+__device__ __forceinline__ int find_member(const int64_t *__restrict__ start, int n, int64_t k) {
+  int lo = 0, hi = n;                          // start[lo] <= k < start[hi]
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (start[mid] <= k) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// Persistent: a grid of a few blocks per SM walks all members' tiles.
+template <int ELEM, typename TT, int BT>
+__global__ void __launch_bounds__(BT)
+batch_element_kernel(const BatchSim *__restrict__ sims, const int32_t *__restrict__ members,
+                     const int64_t *__restrict__ tile_start, int nm, int64_t total, const int32_t *__restrict__ active) {
+  for (int64_t k = blockIdx.x; k < total; k += gridDim.x) {
+    const int j = find_member(tile_start, nm, k);
+    const int sm = members[j];
+    if (active[sm]) {
+      const BatchSim &d = sims[sm];
+      element_tile<ELEM, TT, false, BT>(d.m, d.mc, d.u, d.kh, nullptr, d.m.nel, static_cast<TT *>(d.Ke), d.re,
+                                        k - tile_start[j]);
+    }
+    __syncthreads();
+  }
+}
+
+template <int ND, int NEN, typename TT>
+__global__ void __launch_bounds__(256)
+batch_gather_kernel(const BatchSim *__restrict__ sims, const int32_t *__restrict__ members,
+                    const int64_t *__restrict__ block_start, int nm, const int32_t *__restrict__ active) {
+  const int j = find_member(block_start, nm, blockIdx.x);
+  const int sm = members[j];
+  if (!active[sm]) return;
+  const BatchSim &d = sims[sm];
+  gather_pair<ND, NEN, TT>(d.p, static_cast<const TT *>(d.Ke), d.re, static_cast<TT *>(d.vals), d.rraw, d.rhs,
+                           (blockIdx.x - block_start[j]) * 256 + threadIdx.x);
+}
+
+template <int ND, typename TT>
+__global__ void __launch_bounds__(128)
+batch_precond_kernel(const BatchSim *__restrict__ sims, const int32_t *__restrict__ members,
+                     const int64_t *__restrict__ block_start, int nm, const int32_t *__restrict__ active) {
+  const int j = find_member(block_start, nm, blockIdx.x);
+  const int sm = members[j];
+  if (!active[sm]) return;
+  const BatchSim &d = sims[sm];
+  precond_node<ND, TT>(d.p, static_cast<const TT *>(d.vals), d.precond, static_cast<TT *>(d.minv),
+                       (int32_t)((blockIdx.x - block_start[j]) * 128 + threadIdx.x));
+}
+
+template <int ELEM, typename TT, int BT>
+static cudaError_t launch_batch_element_t(const BatchSim *sims, const int32_t *members, const int64_t *tile_start,
+                                          int nm, int64_t total, const int32_t *active, int grid, cudaStream_t s) {
+  using L = ElemLayout<ELEM, TT, BT>;
+  const size_t smem = L::bytes(false);
+  auto fn = batch_element_kernel<ELEM, TT, BT>;
+  cudaError_t err = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (err != cudaSuccess) return err;
+  fn<<<grid, BT, smem, s>>>(sims, members, tile_start, nm, total, active);
+  return cudaGetLastError();
+}
+
+int batch_tile_elements(int elem, int bt) { return bt / ((elem == LGDM_L2) ? 2 : (elem == LGDM_Q4) ? 4 : 8); }
+
+template <typename TT>
+cudaError_t launch_batch_element(int elem, int bt, const BatchSim *sims, const int32_t *members,
+                                 const int64_t *tile_start, int nm, int64_t total, const int32_t *active, int grid,
+                                 cudaStream_t s) {
+  if (total <= 0) return cudaSuccess;
+#define LGDM_BE(E)                                                                                         \
+  switch (bt) {                                                                                            \
+    case 64: return launch_batch_element_t<E, TT, 64>(sims, members, tile_start, nm, total, active, grid, s);   \
+    case 128: return launch_batch_element_t<E, TT, 128>(sims, members, tile_start, nm, total, active, grid, s); \
+    case 256: return launch_batch_element_t<E, TT, 256>(sims, members, tile_start, nm, total, active, grid, s); \
+  }                                                                                                        \
+  return cudaErrorInvalidValue
+  switch (elem) {
+    case LGDM_L2: LGDM_BE(LGDM_L2);
+    case LGDM_Q4: LGDM_BE(LGDM_Q4);
+    case LGDM_H8: LGDM_BE(LGDM_H8);
+  }
+#undef LGDM_BE
+  return cudaErrorInvalidValue;
+}
+template cudaError_t launch_batch_element<double>(int, int, const BatchSim *, const int32_t *, const int64_t *, int,
+                                                  int64_t, const int32_t *, int, cudaStream_t);
+template cudaError_t launch_batch_element<float>(int, int, const BatchSim *, const int32_t *, const int64_t *, int,
+                                                 int64_t, const int32_t *, int, cudaStream_t);
+
+template <typename TT>
+cudaError_t launch_batch_gather(int elem, const BatchSim *sims, const int32_t *members, const int64_t *block_start,
+                                int nm, int64_t total_blocks, const int32_t *active, cudaStream_t s) {
+  if (total_blocks <= 0) return cudaSuccess;
+  switch (elem) {
+    case LGDM_L2: batch_gather_kernel<2, 2, TT><<<(unsigned)total_blocks, 256, 0, s>>>(sims, members, block_start, nm, active); break;
+    case LGDM_Q4: batch_gather_kernel<3, 4, TT><<<(unsigned)total_blocks, 256, 0, s>>>(sims, members, block_start, nm, active); break;
+    case LGDM_H8: batch_gather_kernel<4, 8, TT><<<(unsigned)total_blocks, 256, 0, s>>>(sims, members, block_start, nm, active); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+template cudaError_t launch_batch_gather<double>(int, const BatchSim *, const int32_t *, const int64_t *, int, int64_t,
+                                                 const int32_t *, cudaStream_t);
+template cudaError_t launch_batch_gather<float>(int, const BatchSim *, const int32_t *, const int64_t *, int, int64_t,
+                                                const int32_t *, cudaStream_t);
+
+template <typename TT>
+cudaError_t launch_batch_precond(int nd, const BatchSim *sims, const int32_t *members, const int64_t *block_start,
+                                 int nm, int64_t total_blocks, const int32_t *active, cudaStream_t s) {
+  if (total_blocks <= 0) return cudaSuccess;
+  switch (nd) {
+    case 2: batch_precond_kernel<2, TT><<<(unsigned)total_blocks, 128, 0, s>>>(sims, members, block_start, nm, active); break;
+    case 3: batch_precond_kernel<3, TT><<<(unsigned)total_blocks, 128, 0, s>>>(sims, members, block_start, nm, active); break;
+    case 4: batch_precond_kernel<4, TT><<<(unsigned)total_blocks, 128, 0, s>>>(sims, members, block_start, nm, active); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+template cudaError_t launch_batch_precond<double>(int, const BatchSim *, const int32_t *, const int64_t *, int, int64_t,
+                                                  const int32_t *, cudaStream_t);
+template cudaError_t launch_batch_precond<float>(int, const BatchSim *, const int32_t *, const int64_t *, int, int64_t,
+                                                 const int32_t *, cudaStream_t);
 
 }  // namespace lgdm

@@ -121,9 +121,9 @@ __device__ __forceinline__ void precond_rows(const TT *__restrict__ minv, const 
   }
 }
 
+// The solver for one system on a group of nb blocks (bid = rank in the group).
 template <int ND, typename TT>
-__global__ void __launch_bounds__(KT) bicgstab_kernel(KrylovArgs A, int mode) {
-  const int nb = gridDim.x, bid = blockIdx.x;
+__device__ __forceinline__ void bicgstab_body(const KrylovArgs &A, const int nb, const int bid, const int mode) {
   const int64_t n0 = (int64_t)bid * A.nnode / nb, n1 = (int64_t)(bid + 1) * A.nnode / nb;
   const int64_t r0 = ND * n0, r1 = ND * n1;
   const TT *vals = static_cast<const TT *>(A.vals);
@@ -300,7 +300,7 @@ __global__ void __launch_bounds__(KT) bicgstab_kernel(KrylovArgs A, int mode) {
         const bool ce = nrm[3] > 0.0 ? nrm[2] <= A.newton_tol * nrm[3] : nrm[2] <= 1e-30;
         // a stalled or broken-down solve can return a tiny increment: never
         // accept it as convergence
-        const bool solved = (mode == 2) ? (A.prior_rel <= KRYLOV_NEWTON_ETA)
+        const bool solved = (mode == 2) ? (A.res->rel_res <= KRYLOV_NEWTON_ETA)
                                         : (status == 0 || rel <= KRYLOV_NEWTON_ETA);
         A.res->converged = (cu && ce && solved) ? 1 : 0;
 #pragma unroll
@@ -322,6 +322,96 @@ __global__ void __launch_bounds__(KT) bicgstab_kernel(KrylovArgs A, int mode) {
     atomicMax(&A.res->status, status);
   }
 }
+
+template <int ND, typename TT>
+__global__ void __launch_bounds__(KT) bicgstab_kernel(KrylovArgs A, int mode) {
+  bicgstab_body<ND, TT>(A, gridDim.x, blockIdx.x, mode);
+}
+
+// Several independent systems in one cooperative launch: block b belongs to
+// the system s with group_start[s] <= b < group_start[s+1]; every system has
+// its own barrier words and partial sums, so its arithmetic and its result
+// are those of a launch of its group size alone.
+template <int ND, typename TT>
+__global__ void __launch_bounds__(KT) bicgstab_grouped_kernel(const KrylovArgs *__restrict__ args,
+                                                              const int32_t *__restrict__ members,
+                                                              const int32_t *__restrict__ group_start,
+                                                              const int32_t *__restrict__ active, int nsys,
+                                                              int mode) {
+  int lo = 0, hi = nsys;                       // group_start[lo] <= b < group_start[hi]
+  const int b = blockIdx.x;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (group_start[mid] <= b) lo = mid;
+    else hi = mid;
+  }
+  const int sm = members[lo];
+  if (!active[sm]) return;
+  const KrylovArgs A = args[sm];
+  bicgstab_body<ND, TT>(A, group_start[lo + 1] - group_start[lo], b - group_start[lo], mode);
+}
+
+// Zero the barrier words and the status of every active member before a grouped launch.
+__global__ void reset_members_kernel(const KrylovArgs *__restrict__ args, const int32_t *__restrict__ members,
+                                     const int32_t *__restrict__ active, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int sm = members[i];
+  if (!active[sm]) return;
+  args[sm].bar_count[0] = 0u;
+  args[sm].bar_gen[0] = 0u;
+  args[sm].res->status = 0;
+}
+
+// Copy every member's result block into one array (one copy to the host).
+__global__ void collect_results_kernel(const KrylovArgs *__restrict__ args, int n, SolveResult *__restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = *args[i].res;
+}
+
+cudaError_t launch_collect_results(const KrylovArgs *d_args, int n, SolveResult *d_out, cudaStream_t s) {
+  collect_results_kernel<<<(n + 127) / 128, 128, 0, s>>>(d_args, n, d_out);
+  return cudaGetLastError();
+}
+
+template <typename TT>
+cudaError_t launch_bicgstab_grouped(int nd, const KrylovArgs *d_args, const int32_t *d_members,
+                                    const int32_t *d_group_start, const int32_t *d_active, int nsys,
+                                    int total_blocks, int mode, cudaStream_t s) {
+  reset_members_kernel<<<(nsys + 127) / 128, 128, 0, s>>>(d_args, d_members, d_active, nsys);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  int ns = nsys;
+  void *params[] = {(void *)&d_args, (void *)&d_members, (void *)&d_group_start, (void *)&d_active, &ns, &mode};
+  const void *fn = nullptr;
+  switch (nd) {
+    case 2: fn = (const void *)bicgstab_grouped_kernel<2, TT>; break;
+    case 3: fn = (const void *)bicgstab_grouped_kernel<3, TT>; break;
+    case 4: fn = (const void *)bicgstab_grouped_kernel<4, TT>; break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaLaunchCooperativeKernel(fn, dim3(total_blocks), dim3(KT), params, 0, s);
+}
+template cudaError_t launch_bicgstab_grouped<double>(int, const KrylovArgs *, const int32_t *, const int32_t *,
+                                                     const int32_t *, int, int, int, cudaStream_t);
+template cudaError_t launch_bicgstab_grouped<float>(int, const KrylovArgs *, const int32_t *, const int32_t *,
+                                                    const int32_t *, int, int, int, cudaStream_t);
+
+template <typename TT>
+int bicgstab_grouped_max_blocks() {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  int p2 = 0, p3 = 0, p4 = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p2, bicgstab_grouped_kernel<2, TT>, KT, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p3, bicgstab_grouped_kernel<3, TT>, KT, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p4, bicgstab_grouped_kernel<4, TT>, KT, 0);
+  int per = p2 < p3 ? p2 : p3;
+  per = per < p4 ? per : p4;
+  return per * sms;
+}
+template int bicgstab_grouped_max_blocks<double>();
+template int bicgstab_grouped_max_blocks<float>();
 
 template <typename TT>
 int bicgstab_max_blocks() {
@@ -453,6 +543,7 @@ __global__ void __launch_bounds__(KT) gmres_kernel(KrylovArgs A, GmresArgs G) {
       s_g[0] = beta;
       for (int i = 1; i <= m; ++i) s_g[i] = 0.0;
     }
+    __syncthreads();              // the preconditioner reads whole nodes: rows of other threads
     int k = 0;
     for (int j = 0; j < m && it < A.max_iter; ++j) {
       ++it;

@@ -105,6 +105,31 @@ cudaError_t launch_damage_field(const MatConst &mc, const double *kappa_hist, in
 cudaError_t launch_reaction_sum(const double *re, const int32_t *idx, const double *w, int32_t n,
                                 double *out, cudaStream_t s);
 
+// One member of a batch, as the batched kernels see it.
+struct BatchSim {
+  MeshView m;
+  MatConst mc;
+  const double *u, *kh;
+  void *Ke;
+  double *re;
+  PatternView p;
+  void *vals;
+  double *rraw, *rhs;
+  void *minv;
+  int32_t precond;
+};
+int batch_tile_elements(int elem, int bt);
+template <typename TT>
+cudaError_t launch_batch_element(int elem, int bt, const BatchSim *sims, const int32_t *members,
+                                 const int64_t *tile_start, int nm, int64_t total, const int32_t *active, int grid,
+                                 cudaStream_t s);
+template <typename TT>
+cudaError_t launch_batch_gather(int elem, const BatchSim *sims, const int32_t *members, const int64_t *block_start,
+                                int nm, int64_t total_blocks, const int32_t *active, cudaStream_t s);
+template <typename TT>
+cudaError_t launch_batch_precond(int nd, const BatchSim *sims, const int32_t *members, const int64_t *block_start,
+                                 int nm, int64_t total_blocks, const int32_t *active, cudaStream_t s);
+
 constexpr int KRYLOV_THREADS = 256;
 
 struct KrylovArgs {
@@ -112,7 +137,6 @@ struct KrylovArgs {
   int32_t max_iter;
   int32_t stall_iters;        // stop after this many iterations without a new best residual
   double rtol, newton_tol;
-  double prior_rel;           // mode 2: relative residual of the solve that produced x
   PatternView p;
   const void *vals;           // TT [nnz]
   const void *minv;           // TT [nnode*nd*nd]
@@ -128,6 +152,14 @@ template <typename TT>
 cudaError_t launch_bicgstab(const KrylovArgs &a, int nblocks, int mode, cudaStream_t s);
 template <typename TT>
 int bicgstab_max_blocks();
+// one cooperative launch over several systems (block groups, see krylov.cu)
+template <typename TT>
+cudaError_t launch_bicgstab_grouped(int nd, const KrylovArgs *d_args, const int32_t *d_members,
+                                    const int32_t *d_group_start, const int32_t *d_active, int nsys,
+                                    int total_blocks, int mode, cudaStream_t s);
+cudaError_t launch_collect_results(const KrylovArgs *d_args, int n, SolveResult *d_out, cudaStream_t s);
+template <typename TT>
+int bicgstab_grouped_max_blocks();
 
 constexpr int GMRES_MAX_M = 128;
 struct GmresArgs {

@@ -67,7 +67,7 @@ def workspace_bytes(mesh, **opts) -> int:
 
 
 class Sim:
-    def __init__(self, mesh, material, bcs, device=None, stream=None, **opts):
+    def __init__(self, mesh, material, bcs, device=None, stream=None, fill_workspace=None, **opts):
         lib = L.load()
         self._lib = lib
         self.h = None
@@ -82,6 +82,8 @@ class Sim:
         L.check(lib.lgdm_workspace_size(C.byref(m.s), C.byref(self.options), C.byref(n)))
         self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
         self.workspace = torch.empty(int(n.value), dtype=torch.uint8, device=self.device)
+        if fill_workspace is not None:                 # debugging aid: poison the workspace
+            self.workspace.fill_(int(fill_workspace))
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
         h = C.c_void_p()
         with torch.cuda.device(self.device):
