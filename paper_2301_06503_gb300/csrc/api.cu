@@ -334,15 +334,18 @@ int max_krylov_blocks(bool fp32) {
   return v;
 }
 
-// Krylov grid: co-resident blocks, about two nodes' rows per thread at most.
+// Krylov grid: one node per thread, and as many co-resident blocks as keep
+// at least 16 nodes each -- the FP64 pipe of an SM (2 FMA per clock on this
+// part) must not carry a small system alone.
 int choose_krylov_blocks(const lgdm_sim &s, bool query_device) {
-  int want = (int)((s.ndof + 2 * KRYLOV_THREADS - 1) / (2 * KRYLOV_THREADS));
-  if (want < 1) want = 1;
-  int cap = 152 * 4;
+  int cap = 152 * 2;
   if (query_device) {
     const int m = max_krylov_blocks(s.opt.precision == LGDM_PREC_FP32_TANGENT);
     if (m > 0) cap = m;
   }
+  int want = (int)std::max<int64_t>((s.nnode + KRYLOV_THREADS - 1) / KRYLOV_THREADS,
+                                    std::min<int64_t>(cap, (s.nnode + 15) / 16));
+  if (want < 1) want = 1;
   if (s.opt.krylov_blocks > 0) want = s.opt.krylov_blocks;
   return std::min(want, cap);
 }

@@ -38,9 +38,10 @@ __device__ bool grid_barrier(unsigned int *count, unsigned int *gen, unsigned in
   __syncthreads();
   if (threadIdx.x == 0) {
     cuda::atomic_ref<unsigned int, cuda::thread_scope_device> c(*count), g(*gen);
+    // the block's writes reach thread 0 through __syncthreads; its release
+    // (cumulative) publishes them, the acquire below receives the others'
     const unsigned int my_gen = g.load(cuda::memory_order_acquire);
     int ok = 1;
-    __threadfence();
     if (c.fetch_add(1u, cuda::memory_order_acq_rel) == nblocks - 1) {
       c.store(0u, cuda::memory_order_relaxed);
       g.fetch_add(1u, cuda::memory_order_release);
@@ -49,10 +50,8 @@ __device__ bool grid_barrier(unsigned int *count, unsigned int *gen, unsigned in
       unsigned int spins = 0;
       while (g.load(cuda::memory_order_acquire) == my_gen) {
         if ((++spins & 255u) == 0 && globaltimer() - t0 > BARRIER_NS) { ok = 0; break; }
-        __nanosleep(32);
       }
     }
-    __threadfence();
     s_ok = ok;
   }
   __syncthreads();
@@ -121,11 +120,49 @@ __device__ __forceinline__ void precond_rows(const TT *__restrict__ minv, const 
   }
 }
 
+// y = K x for the nd rows of node a.  One neighbour index and nd values of
+// x feed nd*nd products, accumulated in double.  x is written by other
+// blocks during the launch, so it is read through L2 (__ldcg).
+template <int ND, typename TT>
+__device__ __forceinline__ void spmv_node(const PatternView &p, const TT *__restrict__ vals, const double *x,
+                                          int64_t a, double *y) {
+  const int32_t pb = p.nbr_ptr[a], deg = p.nbr_ptr[a + 1] - pb;
+  const TT *v = vals + (int64_t)ND * ND * pb;
+  const int64_t rs = (int64_t)ND * deg;           // stride between the node's rows
+#pragma unroll
+  for (int i = 0; i < ND; ++i) y[i] = 0.0;
+#pragma unroll 3
+  for (int32_t s = 0; s < deg; ++s) {
+    const double *xb = x + (int64_t)ND * p.nbr[pb + s];
+    double xv[ND];
+#pragma unroll
+    for (int j = 0; j < ND; ++j) xv[j] = __ldcg(xb + j);
+#pragma unroll
+    for (int i = 0; i < ND; ++i)
+#pragma unroll
+      for (int j = 0; j < ND; ++j) y[i] += (double)v[i * rs + ND * s + j] * xv[j];
+  }
+}
+
+// out = M^-1 in for node a (stored in TT, applied in double).
+template <int ND, typename TT>
+__device__ __forceinline__ void precond_apply(const TT *__restrict__ minv, int64_t a, const double *in, double *out) {
+  const TT *m = minv + a * ND * ND;
+#pragma unroll
+  for (int i = 0; i < ND; ++i) {
+    double s = 0.0;
+#pragma unroll
+    for (int j = 0; j < ND; ++j) s += (double)m[i * ND + j] * in[j];
+    out[i] = s;
+  }
+}
+
 // The solver for one system on a group of nb blocks (bid = rank in the group).
+// A thread owns whole nodes: their nd rows in every vector, the node-block
+// preconditioner and the SpMV rows.
 template <int ND, typename TT>
 __device__ __forceinline__ void bicgstab_body(const KrylovArgs &A, const int nb, const int bid, const int mode) {
   const int64_t n0 = (int64_t)bid * A.nnode / nb, n1 = (int64_t)(bid + 1) * A.nnode / nb;
-  const int64_t r0 = ND * n0, r1 = ND * n1;
   const TT *vals = static_cast<const TT *>(A.vals);
   const TT *minv = static_cast<const TT *>(A.minv);
   double *P = A.partial;                      // [3 slots][4 values][nb]
@@ -134,6 +171,7 @@ __device__ __forceinline__ void bicgstab_body(const KrylovArgs &A, const int nb,
     const double s = block_sum(v);
     if (threadIdx.x == 0) __stcg(part(slot, k) + bid, s);
   };
+#define LGDM_NODES for (int64_t a = n0 + threadIdx.x; a < n1; a += KT)
   int status = 1, it = 0;
   double rel = 0.0, bnorm = 0.0;
   double rho = 0.0, alpha = 1.0, omega = 1.0, rho_old = 1.0;
@@ -143,11 +181,15 @@ __device__ __forceinline__ void bicgstab_body(const KrylovArgs &A, const int nb,
   if (mode != 2) {
     // bnorm = ||b||; x = 0
     double l = 0.0;
-    for (int64_t row = r0 + threadIdx.x; row < r1; row += KT) {
-      const double b = A.rhs[row];
-      A.x[row] = 0.0;
-      A.xb[row] = 0.0;
-      l += b * b;
+    LGDM_NODES {
+#pragma unroll
+      for (int i = 0; i < ND; ++i) {
+        const int64_t row = ND * a + i;
+        const double b = A.rhs[row];
+        A.x[row] = 0.0;
+        A.xb[row] = 0.0;
+        l += b * b;
+      }
     }
     publish(2, 0, l);
     ok = grid_barrier(A.bar_count, A.bar_gen, nb);
@@ -161,17 +203,26 @@ __device__ __forceinline__ void bicgstab_body(const KrylovArgs &A, const int nb,
       if (fresh) {
         // (re)start: r = b - K x (the true residual), shadow residual r0 = r
         if (restarts > 0) {
-          for (int64_t row = r0 + threadIdx.x; row < r1; row += KT) A.ph[row] = A.x[row];
+          LGDM_NODES {
+#pragma unroll
+            for (int i = 0; i < ND; ++i) A.ph[ND * a + i] = A.x[ND * a + i];
+          }
           if (!(ok = grid_barrier(A.bar_count, A.bar_gen, nb))) break;
         }
         double lrr = 0.0;
-        for (int64_t row = r0 + threadIdx.x; row < r1; row += KT) {
-          const double rn = A.rhs[row] - (restarts > 0 ? spmv_row<ND, TT>(A.p, vals, A.ph, row) : 0.0);
-          A.r[row] = rn;
-          A.r0[row] = rn;
-          A.pv[row] = 0.0;
-          A.v[row] = 0.0;
-          lrr += rn * rn;
+        LGDM_NODES {
+          double y[ND];
+          if (restarts > 0) spmv_node<ND, TT>(A.p, vals, A.ph, a, y);
+#pragma unroll
+          for (int i = 0; i < ND; ++i) {
+            const int64_t row = ND * a + i;
+            const double rn = A.rhs[row] - (restarts > 0 ? y[i] : 0.0);
+            A.r[row] = rn;
+            A.r0[row] = rn;
+            A.pv[row] = 0.0;
+            A.v[row] = 0.0;
+            lrr += rn * rn;
+          }
         }
         publish(2, 0, lrr);
         if (!(ok = grid_barrier(A.bar_count, A.bar_gen, nb))) break;
@@ -180,7 +231,10 @@ __device__ __forceinline__ void bicgstab_body(const KrylovArgs &A, const int nb,
         if (!isfinite(rho)) { status = 3; break; }
         if (rel < best) {                       // the true residual of x: keep x as the best iterate
           best = rel;
-          for (int64_t row = r0 + threadIdx.x; row < r1; row += KT) A.xb[row] = A.x[row];
+          LGDM_NODES {
+#pragma unroll
+            for (int i = 0; i < ND; ++i) A.xb[ND * a + i] = A.x[ND * a + i];
+          }
         }
         if (rel <= A.rtol) { status = 0; break; }
         if (verify && restarts >= KRYLOV_MAX_RESTARTS) { status = 1; break; }
@@ -193,16 +247,29 @@ __device__ __forceinline__ void bicgstab_body(const KrylovArgs &A, const int nb,
       ++it;
       const double beta = first ? 0.0 : (rho / rho_old) * (alpha / omega);
       first = false;
-      for (int64_t row = r0 + threadIdx.x; row < r1; row += KT)
-        A.pv[row] = A.r[row] + beta * (A.pv[row] - omega * A.v[row]);
-      __syncthreads();
-      precond_rows<ND, TT>(minv, A.pv, A.ph, r0, r1);
+      // p = r + beta (p - omega v); phat = M^-1 p
+      LGDM_NODES {
+        double pv[ND], ph[ND];
+#pragma unroll
+        for (int i = 0; i < ND; ++i) {
+          const int64_t row = ND * a + i;
+          pv[i] = A.r[row] + beta * (A.pv[row] - omega * A.v[row]);
+          A.pv[row] = pv[i];
+        }
+        precond_apply<ND, TT>(minv, a, pv, ph);
+#pragma unroll
+        for (int i = 0; i < ND; ++i) A.ph[ND * a + i] = ph[i];
+      }
       if (!(ok = grid_barrier(A.bar_count, A.bar_gen, nb))) break;
       double l1 = 0.0;
-      for (int64_t row = r0 + threadIdx.x; row < r1; row += KT) {
-        const double vv = spmv_row<ND, TT>(A.p, vals, A.ph, row);
-        A.v[row] = vv;
-        l1 += A.r0[row] * vv;
+      LGDM_NODES {
+        double y[ND];
+        spmv_node<ND, TT>(A.p, vals, A.ph, a, y);
+#pragma unroll
+        for (int i = 0; i < ND; ++i) {
+          A.v[ND * a + i] = y[i];
+          l1 += A.r0[ND * a + i] * y[i];
+        }
       }
       publish(0, 0, l1);
       if (!(ok = grid_barrier(A.bar_count, A.bar_gen, nb))) break;
@@ -215,16 +282,30 @@ __device__ __forceinline__ void bicgstab_body(const KrylovArgs &A, const int nb,
         continue;
       }
       alpha = rho / r0v;
-      for (int64_t row = r0 + threadIdx.x; row < r1; row += KT) A.sv[row] = A.r[row] - alpha * A.v[row];
-      __syncthreads();
-      precond_rows<ND, TT>(minv, A.sv, A.sh, r0, r1);
+      // s = r - alpha v; shat = M^-1 s
+      LGDM_NODES {
+        double sv[ND], sh[ND];
+#pragma unroll
+        for (int i = 0; i < ND; ++i) {
+          const int64_t row = ND * a + i;
+          sv[i] = A.r[row] - alpha * A.v[row];
+          A.sv[row] = sv[i];
+        }
+        precond_apply<ND, TT>(minv, a, sv, sh);
+#pragma unroll
+        for (int i = 0; i < ND; ++i) A.sh[ND * a + i] = sh[i];
+      }
       if (!(ok = grid_barrier(A.bar_count, A.bar_gen, nb))) break;
       double lts = 0.0, ltt = 0.0;
-      for (int64_t row = r0 + threadIdx.x; row < r1; row += KT) {
-        const double tv = spmv_row<ND, TT>(A.p, vals, A.sh, row);
-        A.t[row] = tv;
-        lts += tv * A.sv[row];
-        ltt += tv * tv;
+      LGDM_NODES {
+        double y[ND];
+        spmv_node<ND, TT>(A.p, vals, A.sh, a, y);
+#pragma unroll
+        for (int i = 0; i < ND; ++i) {
+          A.t[ND * a + i] = y[i];
+          lts += y[i] * A.sv[ND * a + i];
+          ltt += y[i] * y[i];
+        }
       }
       publish(1, 0, lts);
       publish(1, 1, ltt);
@@ -232,12 +313,16 @@ __device__ __forceinline__ void bicgstab_body(const KrylovArgs &A, const int nb,
       const double ts = grid_sum(part(1, 0), nb), tt = grid_sum(part(1, 1), nb);
       omega = (tt > 0.0) ? ts / tt : 0.0;
       double lrr = 0.0, lrho = 0.0;
-      for (int64_t row = r0 + threadIdx.x; row < r1; row += KT) {
-        A.x[row] += alpha * A.ph[row] + omega * A.sh[row];
-        const double rn = A.sv[row] - omega * A.t[row];
-        A.r[row] = rn;
-        lrr += rn * rn;
-        lrho += A.r0[row] * rn;
+      LGDM_NODES {
+#pragma unroll
+        for (int i = 0; i < ND; ++i) {
+          const int64_t row = ND * a + i;
+          A.x[row] += alpha * A.ph[row] + omega * A.sh[row];
+          const double rn = A.sv[row] - omega * A.t[row];
+          A.r[row] = rn;
+          lrr += rn * rn;
+          lrho += A.r0[row] * rn;
+        }
       }
       publish(2, 0, lrr);
       publish(2, 1, lrho);
@@ -250,7 +335,10 @@ __device__ __forceinline__ void bicgstab_body(const KrylovArgs &A, const int nb,
       if (rel < best) {
         best = rel;
         since_best = 0;
-        for (int64_t row = r0 + threadIdx.x; row < r1; row += KT) A.xb[row] = A.x[row];
+        LGDM_NODES {
+#pragma unroll
+          for (int i = 0; i < ND; ++i) A.xb[ND * a + i] = A.x[ND * a + i];
+        }
       } else if (++since_best > A.stall_iters) {   // no progress: stop with the best iterate
         status = 1;
         break;
@@ -266,24 +354,29 @@ __device__ __forceinline__ void bicgstab_body(const KrylovArgs &A, const int nb,
     }
   }
   if (ok && mode != 2 && status != 0 && status != 3 && bnorm > 0.0) {
-    // not converged: return the best iterate (its recursive residual may be
-    // an underestimate of the true one by the drift BiCGSTAB accumulates)
-    __syncthreads();
-    for (int64_t row = r0 + threadIdx.x; row < r1; row += KT) A.x[row] = A.xb[row];
+    // not converged: return the best iterate
+    LGDM_NODES {
+#pragma unroll
+      for (int i = 0; i < ND; ++i) A.x[ND * a + i] = A.xb[ND * a + i];
+    }
     rel = best;
   }
   if (ok && mode != 0 && status != 3) {
     double ldu = 0.0, lu = 0.0, lde = 0.0, le = 0.0;
-    for (int64_t row = r0 + threadIdx.x; row < r1; row += KT) {
-      const double d = A.x[row];
-      const double un = A.u[row] + d;
-      A.u[row] = un;
-      if (row % ND == ND - 1) {
-        lde += d * d;
-        le += un * un;
-      } else {
-        ldu += d * d;
-        lu += un * un;
+    LGDM_NODES {
+#pragma unroll
+      for (int i = 0; i < ND; ++i) {
+        const int64_t row = ND * a + i;
+        const double d = A.x[row];
+        const double un = A.u[row] + d;
+        A.u[row] = un;
+        if (i == ND - 1) {
+          lde += d * d;
+          le += un * un;
+        } else {
+          ldu += d * d;
+          lu += un * un;
+        }
       }
     }
     publish(0, 0, ldu);
@@ -309,6 +402,7 @@ __device__ __forceinline__ void bicgstab_body(const KrylovArgs &A, const int nb,
       }
     }
   }
+#undef LGDM_NODES
   if (!ok) {
     if (threadIdx.x == 0) atomicMax(&A.res->status, 4);
     return;
