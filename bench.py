@@ -14,6 +14,21 @@ HBM when the timed region starts; L2 is flushed (256 MB write) before each
 step.  The e2e figure drives the same step through the public API from
 pinned host buffers (state in, damage field and reaction out).
 
+Other workloads (--workload): bar (100 two-node elements), beam (200 x 40 x
+40 hexahedra, 1.35M dofs), batch (256 notched plates of 20..300 elements per
+edge in one batch: persistent element kernel, grouped solves, a CUDA graph
+per Newton step, autotuned tiles; a step solves load increment 1 of all of
+them).  --precision fp32 assembles the tangent and applies the
+preconditioner in FP32 (residual, inner products and tests in FP64).
+
+--serving runs the request-serving comparison instead and prints its own
+JSON line: the first --requests requests of the seeded Poisson trace (70 %
+plates, 30 % beams, 20 requests/s), each simulation --serve-steps load
+increments of its 300-increment schedule, served (i) by the continuous-
+batching server with the FP32 tangent and (ii) one at a time in FP64;
+simulations/hour, p50/p99 time-to-solution and service time, and the
+largest difference between the two forms' load-displacement curves.
+
 Usage: python bench.py [--gpus N --steps K --warmup W] [--impl reference]
 Under torchrun each rank runs an independent replica (weak scaling).
 """
@@ -41,11 +56,16 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
-    ap.add_argument("--workload", default="plate", choices=["plate", "bar", "beam"])
+    ap.add_argument("--workload", default="plate", choices=["plate", "bar", "beam", "batch"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--mode", default="loadstep", choices=["loadstep", "newton"],
                     help="loadstep: a step is a converged load increment; newton: one Newton iteration "
                          "(assemble + solve + update), used for profiling captures")
+    ap.add_argument("--serving", action="store_true")
+    ap.add_argument("--requests", type=int, default=16)
+    ap.add_argument("--serve-steps", type=int, default=300)
+    ap.add_argument("--budget-gb", type=float, default=64.0)
+    ap.add_argument("--max-resident", type=int, default=64)
     ap.add_argument("--max-krylov", type=int, default=5000,
                     help="BiCGSTAB iteration cap (profiling captures use a small cap)")
     return ap.parse_args()
@@ -54,10 +74,12 @@ def parse():
 def workload(name):
     import lgdm_inputs as li
     if name == "plate":
-        return li.sen_plate_problem(), "sen_plate_q4_200x200"
+        return [li.sen_plate_problem()], "sen_plate_q4_200x200"
     if name == "bar":
-        return li.bar_problem(), "bar_l2_100"
-    return li.tpb_beam_problem(), "tpb_beam_h8_200x40x40"
+        return [li.bar_problem()], "bar_l2_100"
+    if name == "beam":
+        return [li.tpb_beam_problem()], "tpb_beam_h8_200x40x40"
+    return li.batch_plate_problems(), "batch_256_plates_q4_20to300"
 
 
 def dist_env():
@@ -118,7 +140,7 @@ def peaks():
     return {"hbm_gbs": hbm, "hbm_src": src, "fp64_tflops": 1.25, "fp32_tflops": 75.0}
 
 
-def traffic_for(kernel):
+def traffic_for(kernel, workload):
     """DRAM bytes per launch from a committed ncu summary, if the kernels are unchanged."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
@@ -127,8 +149,8 @@ def traffic_for(kernel):
         rec = json.load(open(path))
         if rec.get("csrc_sha") != csrc_sha():
             return None
-        return rec["kernels"].get(kernel)
-    except (ValueError, KeyError):
+        return rec["kernels"].get(f"{kernel}@{workload}")
+    except (ValueError, KeyError, AttributeError):
         return None
 
 
@@ -140,24 +162,38 @@ def csrc_sha():
     return h.hexdigest()[:16]
 
 
-def cpu_baseline(problem, label, newton_iters=2):
-    """The oracle as it stands: the first Newton iterations of load step 1 (bounded sample)."""
+def _cores_used(cpu_s, wall_s):
+    """Threads the oracle actually kept busy: process CPU time over wall time."""
+    return max(1, int(round(cpu_s / wall_s))) if wall_s > 0 else 1
+
+
+def cpu_baseline(problems, label, newton_iters=2, budget_s=15.0):
+    """The oracle as it stands: the first Newton iterations of load step 1 of
+    each problem in turn until about budget_s of CPU work (bounded sample)."""
     from oracle import assembly as asm
     from oracle import newton as nw
     import scipy.sparse.linalg as spla
-    st = nw.initial_state(problem)
-    u = st.u.copy()
-    u[problem.bcs.dir_dof] = problem.bcs.dir_scale * problem.load(1)
-    t0 = time.perf_counter()
-    for _ in range(newton_iters):
-        K, r = asm.assemble(problem.mesh, problem.material, u, st.kappa_hist)
-        Kb, rb = asm.apply_dirichlet(K, r, problem.bcs.dir_dof)
-        u += spla.spsolve(Kb.tocsc(), -rb)
+    gp, done = 0, 0
+    c0, t0 = os.times(), time.perf_counter()
+    for problem in problems:
+        st = nw.initial_state(problem)
+        u = st.u.copy()
+        u[problem.bcs.dir_dof] = problem.bcs.dir_scale * problem.load(1)
+        for _ in range(newton_iters):
+            K, r = asm.assemble(problem.mesh, problem.material, u, st.kappa_hist)
+            Kb, rb = asm.apply_dirichlet(K, r, problem.bcs.dir_dof)
+            u += spla.spsolve(Kb.tocsc(), -rb)
+        gp += newton_iters * problem.mesh.nel * problem.mesh.ngp
+        done += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
     dt = time.perf_counter() - t0
-    gp = newton_iters * problem.mesh.nel * problem.mesh.ngp
-    return {"value": gp / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{label}: first {newton_iters} Newton iterations of load step 1 "
-                      f"(numpy element integration + scipy SuperLU direct solve), {dt:.1f} s"}
+    c1 = os.times()
+    cpu_s = (c1.user - c0.user) + (c1.system - c0.system)
+    return {"value": gp / dt, "unit": UNIT, "cores": _cores_used(cpu_s, dt), "kind": "oracle",
+            "sample": f"{label}: first {newton_iters} Newton iterations of load step 1 of {done} of "
+                      f"{len(problems)} simulation(s) (numpy element integration + scipy SuperLU direct "
+                      f"solve), {dt:.1f} s wall, {cpu_s:.1f} s CPU"}
 
 
 def run_reference(args):
@@ -169,40 +205,190 @@ def run_reference(args):
     from oracle import newton as nw
     import numpy as np
     import scipy.sparse.linalg as spla
-    p, label = workload(args.workload)
-    st = nw.initial_state(p)
-    u0 = st.u.copy()
-    u0[p.bcs.dir_dof] = p.bcs.dir_scale * p.load(1)
+    probs, label = workload(args.workload)
+    # one Newton iteration per step; the batch workload cycles through its plates
+    states = []
+    for p in probs:
+        st = nw.initial_state(p)
+        u0 = st.u.copy()
+        u0[p.bcs.dir_dof] = p.bcs.dir_scale * p.load(1)
+        states.append((p, u0, st.kappa_hist))
+    k = [0]
 
     def step():
-        K, r = asm.assemble(p.mesh, p.material, u0, st.kappa_hist)
+        p, u0, kh = states[k[0] % len(states)]
+        k[0] += 1
+        K, r = asm.assemble(p.mesh, p.material, u0, kh)
         Kb, rb = asm.apply_dirichlet(K, r, p.bcs.dir_dof)
         du = spla.spsolve(Kb.tocsc(), -rb)
-        return float(np.linalg.norm(du))
+        return p.mesh.nel * p.mesh.ngp
 
     for _ in range(args.warmup):
         step()
-    times = []
+    k[0] = 0
+    times, gp = [], 0
+    c0 = os.times()
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        step()
+        gp += step()
         times.append(time.perf_counter() - t0)
-    gp = p.mesh.nel * p.mesh.ngp
-    value = gp * len(times) / sum(times)
+    c1 = os.times()
+    wall = sum(times)
+    cores = _cores_used((c1.user - c0.user) + (c1.system - c0.system), wall)
+    value = gp / wall
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wall / len(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
             "config": {"workload": label, "step": "one Newton iteration (assemble + direct solve) at load step 1",
                        "l2": "n/a (CPU)"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": f"{label}: {args.steps} Newton iterations at load step 1"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
+class SingleLeg:
+    """One simulation; a step solves load increment 1 from the initial state."""
+
+    def __init__(self, p, label, args):
+        from paper_2301_06503_gb300 import Sim
+        self.p, self.label, self.args = p, label, args
+        self.sim = Sim(p.mesh, p.material, p.bcs, precision=args.precision, max_krylov=args.max_krylov)
+        self.stream = self.sim.stream
+        self.load = p.load(1)
+        self.meshes = [p.mesh]
+
+    def step(self):
+        self.sim.reset_state()
+        if self.args.mode == "newton":
+            self.sim.begin_step(self.load)
+            self.sim.newton_step()
+        else:
+            self.sim.run_step(self.load)
+
+    def start_timing(self):
+        self.sim.enable_timers(True)
+        self.sim.timers(reset=True)
+        self.c0 = self.sim.counters()
+
+    def stop_timing(self):
+        c1 = self.sim.counters()
+        tm = self.sim.timers()
+        m = self.p.mesh
+        newton = c1["assemblies"] - self.c0["assemblies"]
+        sz = self.sim.sizes
+        return {"gp": newton * m.nel * m.ngp, "newton": newton,
+                "krylov_iters": c1["krylov_iters"] - self.c0["krylov_iters"],
+                "halvings": c1["halvings"] - self.c0["halvings"],
+                "launches": c1["kernel_launches"] - self.c0["kernel_launches"],
+                "phase_ms": {k: v[0] for k, v in tm.items()}, "phase_n": {k: v[1] for k, v in tm.items()},
+                "elements": m.nel, "elem": m.elem, "nnode": int(sz.nnode), "nel": m.nel, "nd": int(sz.nd),
+                "nnz": int(sz.nnz), "npairs": int(sz.npairs)}
+
+    def e2e(self, reps):
+        import torch
+        m = self.p.mesh
+        u0 = torch.zeros(m.ndof, dtype=torch.float64).pin_memory().numpy()
+        kh0 = torch.full((m.nel * m.ngp,), self.p.material.kappa0, dtype=torch.float64).pin_memory().numpy()
+        times, gp, dmg = [], 0, None
+        for _ in range(reps):
+            cn0 = self.sim.counters()["assemblies"]
+            t0 = time.perf_counter()
+            self.sim.set_state(u0, kh0)                      # state in (pinned host -> device)
+            if self.args.mode == "newton":
+                self.sim.begin_step(self.load)
+                self.sim.newton_step()
+            else:
+                self.sim.run_step(self.load)
+            dmg = self.sim.field("damage")                   # damage field out
+            self.sim.reaction()                              # load-displacement point out
+            times.append(time.perf_counter() - t0)
+            gp += (self.sim.counters()["assemblies"] - cn0) * m.nel * m.ngp
+        return {"value": gp / sum(times), "unit": UNIT, "h2d_bytes_per_step": int(u0.nbytes + kh0.nbytes),
+                "d2h_bytes_per_step": int(dmg.nbytes + 8)}
+
+    def close(self):
+        self.sim.close()
+
+
+class BatchLeg:
+    """Many simulations in one batch (persistent element kernel, grouped
+    solves, a CUDA graph per Newton step, autotuned tiles); a step solves
+    load increment 1 of every member from its initial state."""
+
+    def __init__(self, problems, label, args):
+        import torch
+        from paper_2301_06503_gb300 import Batch, Sim
+        self.problems, self.label, self.args = problems, label, args
+        self.stream = torch.cuda.Stream()
+        self.sims = [Sim(p.mesh, p.material, p.bcs, stream=self.stream, precision=args.precision,
+                         max_krylov=args.max_krylov) for p in problems]
+        self.batch = Batch(self.sims)
+        self.tuning = self.batch.autotune()
+        self.loads = [p.load(1) for p in problems]
+        self.meshes = [p.mesh for p in problems]
+
+    def step(self):
+        for s in self.sims:
+            s.reset_state()
+        if self.args.mode == "newton":
+            for s, ld in zip(self.sims, self.loads):
+                s.begin_step(ld)
+            self.batch.newton_step()
+        else:
+            self.batch.run_step(self.loads)
+
+    def start_timing(self):
+        self.batch.enable_timers(True)
+        self.batch.timers(reset=True)
+        self.c0 = [s.counters() for s in self.sims]
+
+    def stop_timing(self):
+        c1 = [s.counters() for s in self.sims]
+        tm = self.batch.timers()
+        d = lambda k: sum(b[k] - a[k] for a, b in zip(self.c0, c1))
+        gp = sum((b["assemblies"] - a["assemblies"]) * s.mesh.nel * s.mesh.ngp
+                 for a, b, s in zip(self.c0, c1, self.problems))
+        els = sum(p.mesh.nel for p in self.problems)
+        return {"gp": gp, "newton": d("assemblies"), "krylov_iters": d("krylov_iters"), "halvings": d("halvings"),
+                "launches": d("kernel_launches"),
+                "phase_ms": {k: v[0] for k, v in tm.items()}, "phase_n": {k: v[1] for k, v in tm.items()},
+                "elements": els, "elem": self.problems[0].mesh.elem,
+                "nnode": sum(int(s.sizes.nnode) for s in self.sims), "nel": els,
+                "nd": int(self.sims[0].sizes.nd), "nnz": sum(int(s.sizes.nnz) for s in self.sims),
+                "npairs": sum(int(s.sizes.npairs) for s in self.sims), "tuning": self.tuning}
+
+    def e2e(self, reps):
+        import torch
+        pinned = [(torch.zeros(p.mesh.ndof, dtype=torch.float64).pin_memory().numpy(),
+                   torch.full((p.mesh.nel * p.mesh.ngp,), p.material.kappa0,
+                              dtype=torch.float64).pin_memory().numpy()) for p in self.problems]
+        times, gp, dbytes = [], 0, 0
+        for _ in range(reps):
+            cn0 = [s.counters()["assemblies"] for s in self.sims]
+            t0 = time.perf_counter()
+            for s, (u0, kh0) in zip(self.sims, pinned):
+                s.set_state(u0, kh0)
+            self.batch.run_step(self.loads)
+            dbytes = 0
+            for s in self.sims:
+                dbytes += s.field("damage").nbytes + 8
+                s.reaction()
+            times.append(time.perf_counter() - t0)
+            gp += sum((s.counters()["assemblies"] - a) * p.mesh.nel * p.mesh.ngp
+                      for s, a, p in zip(self.sims, cn0, self.problems))
+        return {"value": gp / sum(times), "unit": UNIT,
+                "h2d_bytes_per_step": int(sum(u.nbytes + k.nbytes for u, k in pinned)),
+                "d2h_bytes_per_step": int(dbytes)}
+
+    def close(self):
+        self.batch.close()
+        for s in self.sims:
+            s.close()
+
+
 def run_ours(args):
-    import numpy as np
     import torch
     world, rank, local = dist_env()
     if world > 1:
@@ -211,36 +397,21 @@ def run_ours(args):
         dist.init_process_group("nccl")
     else:
         torch.cuda.set_device(0)
-    from paper_2301_06503_gb300 import Sim, build, roofline
+    from paper_2301_06503_gb300 import build, roofline
     if rank == 0:
         build()
     if world > 1:
         torch.distributed.barrier()
     build()
-    p, label = workload(args.workload)
-    m = p.mesh
-    sim = Sim(m, p.material, p.bcs, precision=args.precision, max_krylov=args.max_krylov)
-    stream = sim.stream
+    probs, label = workload(args.workload)
+    leg = BatchLeg(probs, label, args) if args.workload == "batch" else SingleLeg(probs[0], label, args)
+    stream = leg.stream
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
-    load = p.load(1)
 
-    if args.mode == "newton":
-        def step():
-            sim.reset_state()
-            sim.begin_step(load)
-            sim.newton_step()
-            return 0.0
-    else:
-        def step():
-            sim.reset_state()
-            sim.run_step(load)
-            return sim.reaction()
-
-    for _ in range(args.warmup):
-        step()
-    sim.enable_timers(True)
-    sim.timers(reset=True)
-    c0 = sim.counters()
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            leg.step()
+    leg.start_timing()
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
@@ -252,112 +423,155 @@ def run_ours(args):
         for k in range(args.steps):
             flush.zero_()
             starts[k].record(stream)
-            step()
+            leg.step()
             ends[k].record(stream)
     torch.cuda.synchronize()
     ck = clocks.stop()
     if world > 1:
         torch.distributed.barrier()
-    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    c1 = sim.counters()
-    tm = sim.timers()
-    newton = c1["assemblies"] - c0["assemblies"]
-    gp = newton * m.nel * m.ngp
+    step_ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
+    st = leg.stop_timing()
     t_s = sum(step_ms) / 1e3
     if world > 1:
         import torch.distributed as dist
-        tt = torch.tensor([t_s, float(gp)], device="cuda", dtype=torch.float64)
+        tt = torch.tensor([t_s, float(st["gp"])], device="cuda", dtype=torch.float64)
         tmax = tt.clone()
         dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
         dist.all_reduce(tt, op=dist.ReduceOp.SUM)
         t_job, gp_job = float(tmax[0]), float(tt[1])
     else:
-        t_job, gp_job = t_s, float(gp)
+        t_job, gp_job = t_s, float(st["gp"])
     value = gp_job / t_job
 
     # ------------------------------------------------ roofline of the dominant kernel
     pk = peaks()
-    tb = 4 if args.precision == "fp32" else 8
-    sz = sim.sizes
-    phase_ms = {k: v[0] for k, v in tm.items()}
-    dom = max(("element", "krylov"), key=lambda k: phase_ms[k])
-    kiters = c1["krylov_iters"] - c0["krylov_iters"]
-    fl_k, by_k = roofline.krylov_iteration(int(sz.nnode), int(sz.nd), int(sz.nnz), int(sz.npairs), tb)
-    res_f, tan_f = roofline.element_flops(m.elem)
+    fp32 = args.precision == "fp32"
+    tb = 4 if fp32 else 8
+    phase_ms, phase_n = st["phase_ms"], st["phase_n"]
+    fl_k, by_k = roofline.krylov_iteration(st["nnode"], st["nd"], st["nnz"], st["npairs"], tb)
+    res_f, tan_f = roofline.element_flops(st["elem"])
+    el_kernel = "batch_element_kernel"
+    kr_kernel = "bicgstab_grouped_kernel"
 
-    def roof_alu(flops_per_launch, ms_per_launch, peak_tf, kernel):
-        ach = flops_per_launch / (ms_per_launch * 1e-3) / 1e12
-        return {"bound": "alu", "achieved": ach, "peak": peak_tf, "unit": "TFLOP/s", "frac": ach / peak_tf,
-                "traffic": traffic_for(kernel), "kernel": kernel,
-                "peak_source": "nominal FP64 pipe of GB300 (1.25 TFLOP/s); an FMA-chain probe measured 1.20"}
-
-    def roof_hbm(bytes_per_launch, ms_per_launch, kernel):
-        ach = bytes_per_launch / (ms_per_launch * 1e-3) / 1e9
-        return {"bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                "frac": ach / pk["hbm_gbs"], "traffic": traffic_for(kernel), "kernel": kernel,
-                "peak_source": pk["hbm_src"]}
-
-    el_ms = phase_ms["element"] / max(tm["element"][1], 1)
-    el_flops = m.nel * (res_f + (tan_f if args.precision == "fp64" else 0))
-    roof_el = roof_alu(el_flops, el_ms, pk["fp64_tflops"], "element_kernel")
-    kr_ms = phase_ms["krylov"] / max(tm["krylov"][1], 1)
-    kr_per_launch = kiters / max(tm["krylov"][1], 1)
-    if args.precision == "fp64":
-        roof_kr = roof_alu(fl_k * kr_per_launch, kr_ms, pk["fp64_tflops"], "bicgstab_kernel")
+    el_ms = phase_ms["element"] / max(phase_n["element"], 1)
+    el_bytes = roofline.assembly_bytes(st["elem"], st["nnode"], st["nel"], st["nnz"], tb)
+    if fp32:
+        # FP64 residual path and FP32 tangent path on separate pipes, bytes on HBM: the slowest bounds
+        cands = {"alu": (st["nel"] * res_f / (pk["fp64_tflops"] * 1e12), st["nel"] * res_f, pk["fp64_tflops"]),
+                 "alu_fp32": (st["nel"] * tan_f / (pk["fp32_tflops"] * 1e12), st["nel"] * tan_f, pk["fp32_tflops"]),
+                 "hbm": (el_bytes / (pk["hbm_gbs"] * 1e9), el_bytes, pk["hbm_gbs"])}
     else:
-        roof_kr = roof_hbm(by_k * kr_per_launch, kr_ms, "bicgstab_kernel")
-    roof = roof_kr if dom == "krylov" else roof_el
+        cands = {"alu": (st["nel"] * (res_f + tan_f) / (pk["fp64_tflops"] * 1e12), st["nel"] * (res_f + tan_f),
+                         pk["fp64_tflops"]),
+                 "hbm": (el_bytes / (pk["hbm_gbs"] * 1e9), el_bytes, pk["hbm_gbs"])}
+    b_el = max(cands, key=lambda k: cands[k][0])
 
-    # ------------------------------------------------ end to end through the public API
-    e2e = None
-    if rank == 0:
-        u0 = torch.zeros(m.ndof, dtype=torch.float64).pin_memory().numpy()
-        kh0 = torch.full((m.nel * m.ngp,), p.material.kappa0, dtype=torch.float64).pin_memory().numpy()
-        e_times, e_gp = [], 0
-        for k in range(max(1, min(args.steps, 5))):
-            cn0 = sim.counters()["assemblies"]
-            t0 = time.perf_counter()
-            sim.set_state(u0, kh0)                           # state in (pinned host -> device)
-            if args.mode == "newton":
-                sim.begin_step(load)
-                sim.newton_step()
-            else:
-                sim.run_step(load)
-            dmg = sim.field("damage")                        # damage field out
-            sim.reaction()                                   # load-displacement point out
-            e_times.append(time.perf_counter() - t0)
-            e_gp += (sim.counters()["assemblies"] - cn0) * m.nel * m.ngp
-        e2e = {"value": e_gp / sum(e_times), "unit": UNIT, "h2d_bytes_per_step": int(u0.nbytes + kh0.nbytes),
-               "d2h_bytes_per_step": int(dmg.nbytes + 8)}
-    sim.close()
+    def roof(bound, work, ms, peak, kernel, note):
+        if bound == "hbm":
+            ach = work / (ms * 1e-3) / 1e9
+            return {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                    "traffic": traffic_for(kernel, label), "kernel": kernel, "peak_source": pk["hbm_src"],
+                    "note": note}
+        ach = work / (ms * 1e-3) / 1e12
+        return {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                "traffic": traffic_for(kernel, label), "kernel": kernel,
+                "peak_source": ("nominal FP64 pipe of GB300 (1.25 TFLOP/s; an FMA-chain probe measured 1.20)"
+                                if peak == pk["fp64_tflops"] else "nominal FP32 pipe of GB300 (75 TFLOP/s)"),
+                "note": note}
 
+    roof_el = roof("hbm" if b_el == "hbm" else "alu", cands[b_el][1], el_ms, cands[b_el][2], el_kernel,
+                   f"element integration of all {st['nel']} elements per launch"
+                   + ("; FP64 residual path on the FP64 pipe (the binding one of FP64 pipe, FP32 pipe, HBM)"
+                      if fp32 else "; FP64 residual and tangent"))
+    kr_ms = phase_ms["krylov"] / max(phase_n["krylov"], 1)
+    kr_per_launch = st["krylov_iters"] / max(phase_n["krylov"], 1)
+    if fp32:
+        roof_kr = roof("hbm", by_k * kr_per_launch, kr_ms, pk["hbm_gbs"], kr_kernel,
+                       f"{kr_per_launch:.0f} BiCGSTAB iterations per launch, algorithmic bytes per iteration {by_k}")
+    else:
+        roof_kr = roof("alu", fl_k * kr_per_launch, kr_ms, pk["fp64_tflops"], kr_kernel,
+                       f"{kr_per_launch:.0f} BiCGSTAB iterations per launch, FP64 flops per iteration {fl_k}")
+    dom = "krylov" if phase_ms["krylov"] >= phase_ms["element"] else "element"
+    roof_dom = roof_kr if dom == "krylov" else roof_el
+
+    e2e = leg.e2e(max(1, min(args.steps, 3))) if rank == 0 else None
+    extra = {"tuning": st["tuning"]} if "tuning" in st else {}
+    leg.close()
     if rank != 0:
         return
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(p, label)
+        cpu = cpu_baseline(probs, label)
+    asm_ms = sum(phase_ms[k] for k in ("element", "gather", "precond")) / max(phase_n["element"], 1)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * t_job / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32-tangent/f64",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if not fp32 else "f32-tangent/f64",
         "data": "synthetic",
-        "config": {"workload": label, "nel": m.nel, "gauss_points": m.nel * m.ngp, "ndof": m.ndof,
-                   "precision": args.precision, "step": "load increment 1 of 500 from the initial state, Newton to convergence",
+        "config": {"workload": label, "simulations": len(probs), "elements": st["elements"],
+                   "gauss_points": sum(m.nel * m.ngp for m in leg.meshes),
+                   "ndof": sum(m.ndof for m in leg.meshes), "precision": args.precision,
+                   "step": ("one Newton iteration from the initial state" if args.mode == "newton" else
+                            "load increment 1 from the initial state, Newton to convergence"),
                    "l2": "flushed (256 MB write) before every step", "parallelism": f"replicas x{world}"},
-        "roofline": roof, "roofline_element": roof_el, "roofline_krylov": roof_kr,
-        "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(c1["kernel_launches"] - c0["kernel_launches"]),
-        "clocks": ck,
-        "detail": {"newton_iters": newton, "krylov_iters": kiters, "halvings": c1["halvings"] - c0["halvings"],
-                   "phase_ms": phase_ms, "phase_launches": {k: v[1] for k, v in tm.items()},
-                   "element_ms_per_launch": el_ms, "assembly_gp_per_s": m.nel * m.ngp / (
-                       (phase_ms["element"] + phase_ms["gather"] + phase_ms["precond"]) / max(tm["element"][1], 1) * 1e-3),
-                   "step_ms": step_ms},
+        "roofline": roof_dom, "roofline_element": roof_el, "roofline_krylov": roof_kr,
+        "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(st["launches"]), "clocks": ck,
+        "detail": {"newton_iters": st["newton"], "krylov_iters": st["krylov_iters"], "halvings": st["halvings"],
+                   "phase_ms": phase_ms, "phase_launches": phase_n, "element_ms_per_launch": el_ms,
+                   "assembly_gp_per_s": sum(m.nel * m.ngp for m in leg.meshes) / (asm_ms * 1e-3) if asm_ms else None,
+                   "step_ms": step_ms, **extra},
     }
+    print(json.dumps(line), flush=True)
+
+
+def run_serving(args):
+    """Continuous-batching FP32-tangent serving against one-at-a-time FP64."""
+    import numpy as np
+    import torch
+    import lgdm_inputs as li
+    from paper_2301_06503_gb300 import build
+    from paper_2301_06503_gb300.serve import Job, Server, run_one_at_a_time
+    torch.cuda.set_device(0)
+    build()
+    trace = li.serving_trace(seed=4, count=400, rate=20.0, n_steps=300)[:args.requests]
+
+    def jobs():
+        return [Job(r.seed_index, r.problem, r.arrival, args.serve_steps) for r in trace]
+
+    clocks = Clocks(0)
+    clocks.start()
+    srv = Server(budget_bytes=int(args.budget_gb * (1 << 30)), max_resident=args.max_resident, precision="fp32")
+    js = jobs()
+    rep_b = srv.run(js)
+    js1 = jobs()
+    rep_1 = run_one_at_a_time(js1, precision="fp64")
+    ck = clocks.stop()
+    diff = []
+    for a, b in zip(sorted(js, key=lambda j: j.rid), sorted(js1, key=lambda j: j.rid)):
+        ra, rb = np.asarray(a.reactions), np.asarray(b.reactions)
+        if len(ra) == len(rb) and len(rb):
+            diff.append(float(np.abs(ra - rb).max() / max(np.abs(rb).max(), 1e-300)))
+    line = {"metric": "simulations/hour (served)", "value": rep_b["sims_per_hour"], "unit": "sims/h",
+            "higher_is_better": True, "n_gpus": 1, "data": "synthetic",
+            "config": {"workload": "serving_mix", "requests": len(trace),
+                       "plates": sum(1 for r in trace if r.problem.mesh.elem == 2),
+                       "beams": sum(1 for r in trace if r.problem.mesh.elem == 3),
+                       "elements": [int(r.problem.mesh.nel) for r in trace],
+                       "load_steps_per_sim": args.serve_steps, "schedule": "300 increments to the final load",
+                       "arrivals": "Poisson 20/s, seed 4", "budget_gb": args.budget_gb,
+                       "max_resident": args.max_resident},
+            "served_fp32_batched": rep_b, "one_at_a_time_fp64": rep_1,
+            "speedup_sims_per_hour": rep_b["sims_per_hour"] / rep_1["sims_per_hour"] if rep_1["sims_per_hour"] else None,
+            "curve_max_rel_diff_fp32_vs_fp64": max(diff) if diff else None,
+            "tuning": srv.tuning, "clocks": ck}
     print(json.dumps(line), flush=True)
 
 
 def main():
     args = parse()
+    if args.serving:
+        run_serving(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -221,6 +221,12 @@ lgdm_status lgdm_reset_timers(lgdm_sim *sim);
  * [5] increment halvings.  n entries are written (n <= 6). */
 lgdm_status lgdm_get_counters(const lgdm_sim *sim, int64_t *counters, int32_t n);
 
+/* Stored energy Psi (Eq. 1) integrated over the mesh at the current state,
+ * with the trial history max(kappa_hist, ebar) (at a committed state this is
+ * kappa_hist).  Uses the assembly scratch: call it between load steps.
+ * Synchronises. */
+lgdm_status lgdm_get_energy(lgdm_sim *sim, double *psi);
+
 /* Reaction at the last committed state.  Synchronises. */
 lgdm_status lgdm_get_reaction(lgdm_sim *sim, double *reaction);
 
@@ -257,6 +263,16 @@ lgdm_status lgdm_batch_get_tuning(const lgdm_batch *batch, int32_t *block_thread
 lgdm_status lgdm_batch_autotune(lgdm_batch *batch, int32_t *block_threads, int32_t *grid_factor, double *ms);
 /* Batched assembly of the members with active[i] != 0 (host array of n). */
 lgdm_status lgdm_batch_assemble(lgdm_batch *batch, const int32_t *active);
+/* Phase timers of a batch: CUDA events on the batch stream around the
+ * element launches, the gathers, the preconditioner set-ups and the first
+ * (mode 0) grouped solve of every Newton step, in that order (also inside a
+ * captured graph; turning timers on or off drops the graph so that the next
+ * step captures it again).  get_timers returns the summed milliseconds and
+ * the number of timed steps per phase {element, gather, precond, krylov};
+ * reset != 0 zeroes them. */
+lgdm_status lgdm_batch_enable_timers(lgdm_batch *batch, int32_t on);
+lgdm_status lgdm_batch_get_timers(lgdm_batch *batch, double *ms4, int64_t *count4, int32_t reset);
+
 /* One Newton iteration (Algorithm 2, lines 6-18) for the active members;
  * converged[i] = 1 converged, 0 not yet, -1 non-finite (host arrays of n,
  * krylov_iters may be NULL).  Synchronises. */

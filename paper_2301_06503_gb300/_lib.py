@@ -81,6 +81,7 @@ _SIGS = {
     "lgdm_commit": (C.c_int, [C.c_void_p]),
     "lgdm_last_solve": (C.c_int, [C.c_void_p, _ip, _ip, _dp, _dp]),
     "lgdm_get_reaction": (C.c_int, [C.c_void_p, _dp]),
+    "lgdm_get_energy": (C.c_int, [C.c_void_p, _dp]),
     "lgdm_enable_timers": (C.c_int, [C.c_void_p, C.c_int32]),
     "lgdm_get_timers": (C.c_int, [C.c_void_p, _dp, C.POINTER(C.c_int64)]),
     "lgdm_reset_timers": (C.c_int, [C.c_void_p]),
@@ -94,6 +95,8 @@ _SIGS = {
     "lgdm_batch_get_tuning": (C.c_int, [C.c_void_p, _ip, _ip, _ip]),
     "lgdm_batch_autotune": (C.c_int, [C.c_void_p, _ip, _ip, _dp]),
     "lgdm_batch_assemble": (C.c_int, [C.c_void_p, _ip]),
+    "lgdm_batch_enable_timers": (C.c_int, [C.c_void_p, C.c_int32]),
+    "lgdm_batch_get_timers": (C.c_int, [C.c_void_p, _dp, C.POINTER(C.c_int64), C.c_int32]),
     "lgdm_batch_newton_step": (C.c_int, [C.c_void_p, _ip, _ip, _ip]),
     "lgdm_batch_run_step": (C.c_int, [C.c_void_p, _dp, _ip, _ip]),
     "lgdm_solve_noalloc": (C.c_int, [C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,

@@ -86,3 +86,15 @@ class Batch:
                                                its.ctypes.data_as(C.POINTER(C.c_int32)),
                                                st.ctypes.data_as(C.POINTER(C.c_int32))))
         return its, st
+
+    PHASES = ("element", "gather", "precond", "krylov")
+
+    def enable_timers(self, on=True):
+        self._ck(self._lib.lgdm_batch_enable_timers(self.h, 1 if on else 0))
+
+    def timers(self, reset=False):
+        """{phase: (milliseconds, timed Newton steps)} for element, gather, precond, krylov."""
+        ms = (C.c_double * 4)()
+        n = (C.c_int64 * 4)()
+        self._ck(self._lib.lgdm_batch_get_timers(self.h, ms, n, 1 if reset else 0))
+        return {k: (ms[i], n[i]) for i, k in enumerate(self.PHASES)}

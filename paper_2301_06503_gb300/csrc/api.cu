@@ -313,8 +313,8 @@ void carve(lgdm_sim &s, Carver &c) {
     s.gm_dots = c.take<double>((size_t)(GMRES_MAX_M + 2) * std::max(s.gmres_blocks, 1));
     s.gm_final = c.take<double>(m + 2);
   }
-  s.partial = c.take<double>((size_t)3 * 4 * std::max(s.krylov_blocks, 1));
-  s.field_tmp = c.take<double>(std::max((size_t)s.nel * s.ngp, (size_t)s.ndof));
+  s.partial = c.take<double>((size_t)3 * 4 * krylov_ntiles(s.nnode));
+  s.field_tmp = c.take<double>(std::max((size_t)s.nel * s.ngp, (size_t)s.ndof) + 64);   // + energy block sums
   s.reaction = c.take<double>(1);
   s.bar = c.take<unsigned int>(2);
   s.res = c.take<SolveResult>(1);
@@ -336,18 +336,21 @@ int max_krylov_blocks(bool fp32) {
 
 // Krylov grid: one node per thread, and as many co-resident blocks as keep
 // at least 16 nodes each -- the FP64 pipe of an SM (2 FMA per clock on this
-// part) must not carry a small system alone.
+// part) must not carry a small system alone.  A block owns whole reduction
+// tiles (at most one block per tile) and at most 32 * KRYLOV_MAXW nodes.
 int choose_krylov_blocks(const lgdm_sim &s, bool query_device) {
   int cap = 152 * 2;
   if (query_device) {
     const int m = max_krylov_blocks(s.opt.precision == LGDM_PREC_FP32_TANGENT);
     if (m > 0) cap = m;
   }
-  int want = (int)std::max<int64_t>((s.nnode + KRYLOV_THREADS - 1) / KRYLOV_THREADS,
-                                    std::min<int64_t>(cap, (s.nnode + 15) / 16));
-  if (want < 1) want = 1;
+  int64_t want = std::max<int64_t>((s.nnode + KRYLOV_THREADS - 1) / KRYLOV_THREADS,
+                                   std::min<int64_t>(cap, (s.nnode + 15) / 16));
   if (s.opt.krylov_blocks > 0) want = s.opt.krylov_blocks;
-  return std::min(want, cap);
+  want = std::min<int64_t>(want, krylov_ntiles(s.nnode));
+  want = std::max<int64_t>(want, krylov_min_blocks(s.nnode));
+  if (want < 1) want = 1;
+  return (int)std::min<int64_t>(want, cap);
 }
 
 lgdm_status plan(lgdm_sim &s, const lgdm_mesh &m, const lgdm_options &o, const lgdm_bcs *bcs, Pattern *P,
@@ -371,6 +374,9 @@ lgdm_status plan(lgdm_sim &s, const lgdm_mesh &m, const lgdm_options &o, const l
   s.nnz = pat.npairs * s.nd * s.nd;
   s.ncontrib = (int64_t)s.nel * s.nen * s.nen;
   s.ndir = bcs ? bcs->n_dir : 0;
+  if (krylov_min_blocks(s.nnode) < 1 || krylov_min_blocks(s.nnode) > (query_device ? max_krylov_blocks(
+          o.precision == LGDM_PREC_FP32_TANGENT) : 152 * 16))
+    return fail(nullptr, LGDM_ERR_INVALID_ARG, "mesh too large for one Krylov launch (nodes per block limit)");
   s.krylov_blocks = choose_krylov_blocks(s, query_device);
   s.gmres_blocks = s.krylov_blocks;
   if (query_device && o.gmres_m > 0) {
@@ -785,6 +791,8 @@ KrylovArgs krylov_args(lgdm_sim *s) {
   a.sh = s->kv[8];
   a.xb = s->kv[9];
   a.stall_iters = std::max(500, s->opt.max_krylov / 4);
+  a.tile = krylov_tile(s->nnode);
+  a.ntiles = (int32_t)krylov_ntiles(s->nnode);
   a.u = s->u;
   a.partial = s->partial;
   a.bar_count = s->bar;
@@ -974,6 +982,21 @@ lgdm_status lgdm_get_counters(const lgdm_sim *s, int64_t *c, int32_t n) {
   return LGDM_OK;
 }
 
+lgdm_status lgdm_get_energy(lgdm_sim *s, double *psi) {
+  if (!s || !psi) return fail(s, LGDM_ERR_INVALID_ARG, "NULL argument");
+  // per-Gauss-point values in the element residual scratch, block sums in field_tmp
+  LGDM_CUDA(s, launch_energy(s->elem, s->mesh_view(), s->mc, s->u, s->kappa_hist, s->re, s->field_tmp,
+                             s->field_tmp + ((int64_t)s->nel * s->ngp + 4095) / 4096 + 1, s->stream));
+  double v = 0.0;
+  LGDM_CUDA(s, cudaMemcpyAsync(&v, s->field_tmp + ((int64_t)s->nel * s->ngp + 4095) / 4096 + 1, sizeof(double),
+                               cudaMemcpyDeviceToHost, s->stream));
+  LGDM_CUDA(s, cudaStreamSynchronize(s->stream));
+  s->counters[0] += 3;
+  s->assembled = false;
+  *psi = v;
+  return LGDM_OK;
+}
+
 lgdm_status lgdm_get_reaction(lgdm_sim *s, double *reaction) {
   if (!s || !reaction) return fail(s, LGDM_ERR_INVALID_ARG, "NULL argument");
   LGDM_CUDA(s, cudaMemcpyAsync(reaction, s->reaction, sizeof(double), cudaMemcpyDeviceToHost, s->stream));
@@ -1078,8 +1101,16 @@ struct lgdm_batch {
   std::vector<int32_t> h_active;
   std::vector<SolveResult> h_res;
   std::string err;
+  // phase timers: events before the element launches, after them, after the
+  // gathers, after the preconditioner set-ups and after the first solve
+  bool timers_on = false;
+  cudaEvent_t tev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  double t_ms[4] = {0, 0, 0, 0};
+  int64_t t_n[4] = {0, 0, 0, 0};
   ~lgdm_batch() {
     if (graph) cudaGraphExecDestroy(graph);
+    for (auto e : tev)
+      if (e) cudaEventDestroy(e);
   }
 };
 
@@ -1103,28 +1134,59 @@ lgdm_status bfail(lgdm_batch *b, lgdm_status st, const std::string &m) {
     if (_e != cudaSuccess) return bfail(b, LGDM_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(_e)); \
   } while (0)
 
-// The launches of one batched Newton step up to the solve (mode 0).
+#define LGDM_BMARK(b, k)                                                  \
+  do {                                                                    \
+    if ((b)->timers_on) LGDM_BCUDA(b, cudaEventRecord((b)->tev[k], (b)->stream)); \
+  } while (0)
+
+// The launches of one batched Newton step up to the solve (mode 0): the
+// element launches of every element-type group, then the gathers, then the
+// preconditioner set-ups.
 lgdm_status batch_issue_assembly(lgdm_batch *b) {
   const int grid_cap = b->grid_factor * b->sms;
+  LGDM_BMARK(b, 0);
   for (auto &g : b->groups) {
     const int grid = (int)std::min<int64_t>(g.tiles, grid_cap);
-    if (b->fp32) {
+    if (b->fp32)
       LGDM_BCUDA(b, launch_batch_element<float>(g.elem, b->bt, b->d_sims, g.d_members, g.d_tile, (int)g.members.size(),
                                                 g.tiles, b->d_active, grid, b->stream));
-      LGDM_BCUDA(b, launch_batch_gather<float>(g.elem, b->d_sims, g.d_members, g.d_gblock, (int)g.members.size(),
-                                               g.gblocks, b->d_active, b->stream));
-      LGDM_BCUDA(b, launch_batch_precond<float>(g.nd, b->d_sims, g.d_members, g.d_pblock, (int)g.members.size(),
-                                                g.pblocks, b->d_active, b->stream));
-    } else {
+    else
       LGDM_BCUDA(b, launch_batch_element<double>(g.elem, b->bt, b->d_sims, g.d_members, g.d_tile, (int)g.members.size(),
                                                  g.tiles, b->d_active, grid, b->stream));
+  }
+  LGDM_BMARK(b, 1);
+  for (auto &g : b->groups) {
+    if (b->fp32)
+      LGDM_BCUDA(b, launch_batch_gather<float>(g.elem, b->d_sims, g.d_members, g.d_gblock, (int)g.members.size(),
+                                               g.gblocks, b->d_active, b->stream));
+    else
       LGDM_BCUDA(b, launch_batch_gather<double>(g.elem, b->d_sims, g.d_members, g.d_gblock, (int)g.members.size(),
                                                 g.gblocks, b->d_active, b->stream));
+  }
+  LGDM_BMARK(b, 2);
+  for (auto &g : b->groups) {
+    if (b->fp32)
+      LGDM_BCUDA(b, launch_batch_precond<float>(g.nd, b->d_sims, g.d_members, g.d_pblock, (int)g.members.size(),
+                                                g.pblocks, b->d_active, b->stream));
+    else
       LGDM_BCUDA(b, launch_batch_precond<double>(g.nd, b->d_sims, g.d_members, g.d_pblock, (int)g.members.size(),
                                                  g.pblocks, b->d_active, b->stream));
+  }
+  LGDM_BMARK(b, 3);
+  return LGDM_OK;
+}
+
+// Adds the phase times of the last Newton step (its events have completed).
+void batch_resolve_timers(lgdm_batch *b) {
+  if (!b->timers_on) return;
+  for (int k = 0; k < 4; ++k) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, b->tev[k], b->tev[k + 1]) == cudaSuccess) {
+      b->t_ms[k] += ms;
+      b->t_n[k] += 1;
     }
   }
-  return LGDM_OK;
+  cudaGetLastError();
 }
 
 lgdm_status batch_issue_solve(lgdm_batch *b, int mode) {
@@ -1136,6 +1198,7 @@ lgdm_status batch_issue_solve(lgdm_batch *b, int mode) {
       LGDM_BCUDA(b, launch_bicgstab_grouped<double>(w.nd, b->d_kargs, w.d_members, w.d_start, b->d_active,
                                                     (int)w.members.size(), w.blocks, mode, b->stream));
   }
+  if (mode == 0) LGDM_BMARK(b, 4);
   return LGDM_OK;
 }
 
@@ -1269,29 +1332,57 @@ lgdm_status lgdm_batch_create(lgdm_sim *const *sims, int32_t n, void *ws, size_t
       LGDM_BCUDA(b, cudaMemcpyAsync(g.d_gblock, gb.data(), sizeof(int64_t) * (m + 1), cudaMemcpyHostToDevice, b->stream));
       LGDM_BCUDA(b, cudaMemcpyAsync(g.d_pblock, pbk.data(), sizeof(int64_t) * (m + 1), cudaMemcpyHostToDevice, b->stream));
     }
-    // waves: members with the same nd, each with the block group it uses alone
+    // waves: members with the same nd that fit one co-resident launch
+    // together (each at least its fewest blocks); a wave's blocks are then
+    // shared out in proportion to the members' node counts, so that every
+    // member runs with about the same nodes per thread.  A member's result
+    // does not depend on its block count (tile reductions).
     const int cap = b->fp32 ? bicgstab_grouped_max_blocks<float>() : bicgstab_grouped_max_blocks<double>();
     for (int nd = 2; nd <= 4; ++nd) {
       lgdm_batch::Wave w;
       w.nd = nd;
+      int64_t minsum = 0;
       for (int i = 0; i < n; ++i) {
         lgdm_sim *s = b->sims[i];
         if (s->nd != nd) continue;
-        if (s->krylov_blocks > cap) { delete b; return fail(nullptr, LGDM_ERR_INVALID_ARG, "member Krylov grid too large"); }
-        if (w.blocks + s->krylov_blocks > cap) {
+        const int64_t mb = std::max<int64_t>(1, krylov_min_blocks(s->nnode));
+        if (mb > cap) { delete b; return fail(nullptr, LGDM_ERR_INVALID_ARG, "member Krylov grid too large"); }
+        if (minsum + mb > cap) {
           b->waves.push_back(w);
           w = lgdm_batch::Wave();
           w.nd = nd;
+          minsum = 0;
         }
         w.members.push_back(i);
-        w.blocks += s->krylov_blocks;
+        minsum += mb;
       }
       if (!w.members.empty()) b->waves.push_back(w);
     }
     for (auto &w : b->waves) {
       const int m = (int)w.members.size();
+      int64_t nodes = 0;
+      for (int j = 0; j < m; ++j) nodes += b->sims[w.members[j]]->nnode;
+      std::vector<int64_t> nbk(m), lo(m);
+      int64_t sum = 0;
+      for (int j = 0; j < m; ++j) {
+        lgdm_sim *s = b->sims[w.members[j]];
+        lo[j] = std::max<int64_t>(1, krylov_min_blocks(s->nnode));
+        const int64_t hi = std::max<int64_t>(lo[j], std::min<int64_t>(s->krylov_blocks, krylov_ntiles(s->nnode)));
+        const int64_t share = (int64_t)((double)cap * (double)s->nnode / (double)std::max<int64_t>(nodes, 1));
+        nbk[j] = std::min(hi, std::max(lo[j], share));
+        sum += nbk[j];
+      }
+      while (sum > cap) {                    // trim the largest groups down to their minimum
+        int jm = -1;
+        for (int j = 0; j < m; ++j)
+          if (nbk[j] > lo[j] && (jm < 0 || nbk[j] > nbk[jm])) jm = j;
+        if (jm < 0) break;
+        --nbk[jm];
+        --sum;
+      }
       std::vector<int32_t> st(m + 1, 0);
-      for (int j = 0; j < m; ++j) st[j + 1] = st[j] + b->sims[w.members[j]]->krylov_blocks;
+      for (int j = 0; j < m; ++j) st[j + 1] = st[j] + (int32_t)nbk[j];
+      w.blocks = st[m];
       w.d_members = c.take<int32_t>(m);
       w.d_start = c.take<int32_t>(m + 1);
       LGDM_BCUDA(b, cudaMemcpyAsync(w.d_members, w.members.data(), sizeof(int32_t) * m, cudaMemcpyHostToDevice, b->stream));
@@ -1356,6 +1447,35 @@ lgdm_status lgdm_batch_get_tuning(const lgdm_batch *b, int32_t *block_threads, i
   return LGDM_OK;
 }
 
+lgdm_status lgdm_batch_enable_timers(lgdm_batch *b, int32_t on) {
+  if (!b) return fail(nullptr, LGDM_ERR_INVALID_ARG, "NULL batch");
+  if (on)
+    for (auto &e : b->tev)
+      if (!e) LGDM_BCUDA(b, cudaEventCreate(&e));
+  if ((on != 0) != b->timers_on) {               // the graph holds the event records or not: capture again
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+    b->graph_ok = b->graph_tried = false;
+    b->graph_mode = 0;
+    b->direct_issues = 0;
+  }
+  b->timers_on = on != 0;
+  return LGDM_OK;
+}
+
+lgdm_status lgdm_batch_get_timers(lgdm_batch *b, double *ms, int64_t *count, int32_t reset) {
+  if (!b) return fail(nullptr, LGDM_ERR_INVALID_ARG, "NULL batch");
+  for (int k = 0; k < 4; ++k) {
+    if (ms) ms[k] = b->t_ms[k];
+    if (count) count[k] = b->t_n[k];
+    if (reset) {
+      b->t_ms[k] = 0.0;
+      b->t_n[k] = 0;
+    }
+  }
+  return LGDM_OK;
+}
+
 lgdm_status lgdm_batch_newton_step(lgdm_batch *b, const int32_t *active, int32_t *converged, int32_t *krylov_iters) {
   if (!b || !active) return bfail(b, LGDM_ERR_INVALID_ARG, "NULL argument");
   int nact = 0;
@@ -1370,6 +1490,7 @@ lgdm_status lgdm_batch_newton_step(lgdm_batch *b, const int32_t *active, int32_t
   LGDM_BCUDA(b, launch_collect_results(b->d_kargs, b->n, b->d_res, b->stream));
   LGDM_BCUDA(b, cudaMemcpyAsync(b->h_res.data(), b->d_res, sizeof(SolveResult) * b->n, cudaMemcpyDeviceToHost, b->stream));
   LGDM_BCUDA(b, cudaStreamSynchronize(b->stream));
+  batch_resolve_timers(b);
   // members the first solve left far from its tolerance: GMRES, one by one
   for (int i = 0; i < b->n; ++i) {
     if (!b->h_active[i]) continue;

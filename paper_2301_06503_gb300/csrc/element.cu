@@ -149,7 +149,7 @@ struct ElemLayout {
 
 // One tile of EPB elements: phase 1 and phase 2 for tile `tile` of an
 // element list.  Every thread of the block calls it (it synchronises).
-template <int ELEM, typename TT, bool RES_ONLY, int BT = ELEM_THREADS>
+template <int ELEM, typename TT, bool RES_ONLY, int BT = ELEM_THREADS, bool ENERGY = false>
 __device__ __forceinline__ void element_tile(const MeshView &m, const MatConst &mc, const double *__restrict__ u,
                                              const double *__restrict__ kh, const int32_t *__restrict__ elem_list,
                                              int32_t n_elem, TT *__restrict__ Ke, double *__restrict__ re,
@@ -284,6 +284,16 @@ __device__ __forceinline__ void element_tile(const MeshView &m, const MatConst &
     double ce[NV];
     iso_stress<DIM>(es * mc.lam, es * mc.mu, eps, ce);
     const double omD = 1.0 - D;
+    if constexpr (ENERGY) {
+      // free energy density (Eq. 1) times dV, one value per Gauss point
+      double ece = 0.0, gg = 0.0;
+#pragma unroll
+      for (int v = 0; v < NV; ++v) ece += eps[v] * ce[v];
+#pragma unroll
+      for (int i = 0; i < DIM; ++i) gg += gb[i] * gb[i];
+      const double de = eq - eb;
+      re[slot * NGP + q] = (0.5 * omD * ece + 0.5 * mc.h * de * de + 0.5 * gi * mc.h * mc.c * gg) * dV;
+    }
     double *rd = recD + el * L::RDS + q * L::RD;
 #pragma unroll
     for (int b = 0; b < NEN; ++b)
@@ -325,6 +335,7 @@ __device__ __forceinline__ void element_tile(const MeshView &m, const MatConst &
   }
   __syncthreads();
   if (!valid) return;                                            // no barrier follows in this tile
+  if constexpr (ENERGY) return;
 
   // ---------------- phase 2: block row a
   const double *RD0 = recD + el * L::RDS;
@@ -680,6 +691,59 @@ __global__ void diag_pairs_kernel(PatternView p, int32_t *diag) {
 }
 cudaError_t launch_diag_pairs(const PatternView &p, int32_t *diag, cudaStream_t s) {
   diag_pairs_kernel<<<(p.nnode + 255) / 256, 256, 0, s>>>(p, diag);
+  return cudaGetLastError();
+}
+
+template <int ELEM>
+__global__ void __launch_bounds__(ELEM_THREADS)
+energy_kernel(MeshView m, MatConst mc, const double *__restrict__ u, const double *__restrict__ kh,
+              int32_t n_elem, double *__restrict__ psi) {
+  element_tile<ELEM, double, true, ELEM_THREADS, true>(m, mc, u, kh, nullptr, n_elem, nullptr, psi, blockIdx.x);
+}
+
+// Sum of n values in a fixed order: 256-thread blocks sum fixed chunks in a
+// fixed tree, one block adds the block sums in order.
+__global__ void chunk_sum_kernel(const double *__restrict__ x, int64_t n, int64_t chunk, double *__restrict__ part) {
+  __shared__ double sh[256];
+  const int64_t lo = blockIdx.x * chunk, hi = (lo + chunk < n) ? lo + chunk : n;
+  double s = 0.0;
+  for (int64_t i = lo + threadIdx.x; i < hi; i += 256) s += x[i];
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int off = 128; off > 0; off >>= 1) {
+    if ((int)threadIdx.x < off) sh[threadIdx.x] += sh[threadIdx.x + off];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+}
+
+cudaError_t launch_energy(int elem, const MeshView &m, const MatConst &mc, const double *u, const double *kh,
+                          double *psi, double *part, double *out, cudaStream_t s) {
+  const int nen = (elem == LGDM_L2) ? 2 : (elem == LGDM_Q4) ? 4 : 8;
+  const int epb = ELEM_THREADS / nen;
+  const int grid = (m.nel + epb - 1) / epb;
+  size_t smem = 0;
+  cudaError_t err = cudaSuccess;
+#define LGDM_EN(E)                                                                                   \
+  smem = ElemLayout<E, double>::bytes(true);                                                         \
+  err = cudaFuncSetAttribute(energy_kernel<E>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
+  if (err != cudaSuccess) return err;                                                                \
+  energy_kernel<E><<<grid, ELEM_THREADS, smem, s>>>(m, mc, u, kh, m.nel, psi);                       \
+  break
+  switch (elem) {
+    case LGDM_L2: LGDM_EN(LGDM_L2);
+    case LGDM_Q4: LGDM_EN(LGDM_Q4);
+    case LGDM_H8: LGDM_EN(LGDM_H8);
+    default: return cudaErrorInvalidValue;
+  }
+#undef LGDM_EN
+  err = cudaGetLastError();
+  if (err != cudaSuccess) return err;
+  const int64_t n = (int64_t)m.nel * nen;
+  const int64_t chunk = 4096;
+  const int nblk = (int)((n + chunk - 1) / chunk);
+  chunk_sum_kernel<<<nblk, 256, 0, s>>>(psi, n, chunk, part);
+  chunk_sum_kernel<<<1, 256, 0, s>>>(part, nblk, nblk, out);
   return cudaGetLastError();
 }
 

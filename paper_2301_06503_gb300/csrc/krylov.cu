@@ -5,11 +5,12 @@
 // preconditioner is block-local) and the rows of those nodes.  The CSR
 // values are stored node-block by node-block: the columns of node pair
 // (a, b) are contiguous, so the SpMV reads the node neighbour list instead
-// of a column index per value.  Inner products are summed per block in a
-// fixed tree, published, and after a grid barrier every block adds the
-// per-block partials in the same fixed order: all blocks see bit-identical
-// scalars and the result does not depend on timing.  The grid barrier spins
-// with a time limit and reports a timeout instead of hanging.
+// of a column index per value.  Inner products are summed over fixed node
+// tiles (see krylov_tile), published per tile, and after a grid barrier
+// every block adds the tile sums in the same fixed order: all blocks see
+// bit-identical scalars, and the result depends neither on timing nor on
+// the number of blocks.  The grid barrier spins with a time limit and
+// reports a timeout instead of hanging.
 //
 // mode 1 ends the launch with the Newton update u += delta and the
 // convergence test ||du|| <= tol ||u||, ||de|| <= tol ||e|| (Algorithm 2,
@@ -78,7 +79,7 @@ __device__ double block_sum(double v) {
   return r;
 }
 
-// Sum of the nb published partials, same order in every block.
+// Sum of the nb published partials (tile sums), same order in every block.
 __device__ double grid_sum(const double *part, int nb) {
   double v = 0.0;
   for (int k = threadIdx.x; k < nb; k += KT) v += __ldcg(part + k);
@@ -157,21 +158,63 @@ __device__ __forceinline__ void precond_apply(const TT *__restrict__ minv, int64
   }
 }
 
+// Tile sums of NV per-node quantities over the block's nodes [n0, n1)
+// (tiles [t0, t1) of T nodes): f(a, v) adds node a's terms to v[0..NV).
+// Warp w of chunk c sums nodes n0 + c*KT + 32w .. +31 in a fixed shuffle
+// tree; the tile sum adds its T/32 warp sums in order; tile k's sum of value
+// j goes to out[j * stride + t0 + k].  ws holds 4 * KRYLOV_MAXW doubles.
+template <int NV, typename F>
+__device__ __forceinline__ void reduce_tiles(int64_t n0, int64_t n1, int64_t t0, int64_t t1, int T, double *ws,
+                                             double *out, int64_t stride, F &&f) {
+  __syncthreads();                               // ws may still be read by the previous call
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t len = n1 - n0;
+  const int64_t nch = (len + KT - 1) / KT;
+  const int nwc = (int)((len + 31) / 32);
+  for (int64_t c = 0; c < nch; ++c) {
+    const int64_t a = n0 + c * KT + threadIdx.x;
+    double v[NV];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) v[k] = 0.0;
+    if (a < n1) f(a, v);
+#pragma unroll
+    for (int k = 0; k < NV; ++k)
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+    const int64_t wc = c * (KT / 32) + w;
+    if (lane == 0 && wc < nwc) {
+#pragma unroll
+      for (int k = 0; k < NV; ++k) ws[k * KRYLOV_MAXW + wc] = v[k];
+    }
+  }
+  __syncthreads();
+  const int wpt = T / 32;
+  const int ntl = (int)(t1 - t0);
+  for (int i = threadIdx.x; i < ntl * NV; i += KT) {
+    const int k = i / ntl, tt = i - k * ntl;
+    const int j0 = tt * wpt, j1 = min(j0 + wpt, nwc);
+    double sum = 0.0;
+    for (int j = j0; j < j1; ++j) sum += ws[k * KRYLOV_MAXW + j];
+    __stcg(out + k * stride + t0 + tt, sum);
+  }
+}
+
 // The solver for one system on a group of nb blocks (bid = rank in the group).
 // A thread owns whole nodes: their nd rows in every vector, the node-block
 // preconditioner and the SpMV rows.
 template <int ND, typename TT>
 __device__ __forceinline__ void bicgstab_body(const KrylovArgs &A, const int nb, const int bid, const int mode) {
-  const int64_t n0 = (int64_t)bid * A.nnode / nb, n1 = (int64_t)(bid + 1) * A.nnode / nb;
+  __shared__ double ws[4 * KRYLOV_MAXW];
+  const int T = A.tile;
+  const int64_t NT = A.ntiles;
+  const int64_t t0 = (int64_t)bid * NT / nb, t1 = (int64_t)(bid + 1) * NT / nb;
+  const int64_t n0 = min(t0 * T, (int64_t)A.nnode), n1 = min(t1 * T, (int64_t)A.nnode);
   const TT *vals = static_cast<const TT *>(A.vals);
   const TT *minv = static_cast<const TT *>(A.minv);
-  double *P = A.partial;                      // [3 slots][4 values][nb]
-  auto part = [&](int slot, int k) { return P + ((int64_t)slot * 4 + k) * nb; };
-  auto publish = [&](int slot, int k, double v) {
-    const double s = block_sum(v);
-    if (threadIdx.x == 0) __stcg(part(slot, k) + bid, s);
-  };
+  double *P = A.partial;                      // [3 slots][4 values][ntiles]
+  auto part = [&](int slot, int k) { return P + ((int64_t)slot * 4 + k) * NT; };
 #define LGDM_NODES for (int64_t a = n0 + threadIdx.x; a < n1; a += KT)
+#define LGDM_REDUCE(NV, slot, k0) reduce_tiles<NV>(n0, n1, t0, t1, T, ws, part(slot, k0), NT, [&](int64_t a, double *lv)
   int status = 1, it = 0;
   double rel = 0.0, bnorm = 0.0;
   double rho = 0.0, alpha = 1.0, omega = 1.0, rho_old = 1.0;
@@ -180,21 +223,19 @@ __device__ __forceinline__ void bicgstab_body(const KrylovArgs &A, const int nb,
 
   if (mode != 2) {
     // bnorm = ||b||; x = 0
-    double l = 0.0;
-    LGDM_NODES {
+    LGDM_REDUCE(1, 2, 0) {
 #pragma unroll
       for (int i = 0; i < ND; ++i) {
         const int64_t row = ND * a + i;
         const double b = A.rhs[row];
         A.x[row] = 0.0;
         A.xb[row] = 0.0;
-        l += b * b;
+        lv[0] += b * b;
       }
-    }
-    publish(2, 0, l);
+    });
     ok = grid_barrier(A.bar_count, A.bar_gen, nb);
     if (ok) {
-      bnorm = sqrt(grid_sum(part(2, 0), nb));
+      bnorm = sqrt(grid_sum(part(2, 0), NT));
       if (!(bnorm > 0.0)) status = isfinite(bnorm) ? 0 : 3;
     }
     bool fresh = true, verify = false, first = true;
@@ -209,8 +250,7 @@ __device__ __forceinline__ void bicgstab_body(const KrylovArgs &A, const int nb,
           }
           if (!(ok = grid_barrier(A.bar_count, A.bar_gen, nb))) break;
         }
-        double lrr = 0.0;
-        LGDM_NODES {
+        LGDM_REDUCE(1, 2, 0) {
           double y[ND];
           if (restarts > 0) spmv_node<ND, TT>(A.p, vals, A.ph, a, y);
 #pragma unroll
@@ -221,12 +261,11 @@ __device__ __forceinline__ void bicgstab_body(const KrylovArgs &A, const int nb,
             A.r0[row] = rn;
             A.pv[row] = 0.0;
             A.v[row] = 0.0;
-            lrr += rn * rn;
+            lv[0] += rn * rn;
           }
-        }
-        publish(2, 0, lrr);
+        });
         if (!(ok = grid_barrier(A.bar_count, A.bar_gen, nb))) break;
-        rho = grid_sum(part(2, 0), nb);
+        rho = grid_sum(part(2, 0), NT);
         rel = sqrt(rho) / bnorm;
         if (!isfinite(rho)) { status = 3; break; }
         if (rel < best) {                       // the true residual of x: keep x as the best iterate
@@ -261,19 +300,17 @@ __device__ __forceinline__ void bicgstab_body(const KrylovArgs &A, const int nb,
         for (int i = 0; i < ND; ++i) A.ph[ND * a + i] = ph[i];
       }
       if (!(ok = grid_barrier(A.bar_count, A.bar_gen, nb))) break;
-      double l1 = 0.0;
-      LGDM_NODES {
+      LGDM_REDUCE(1, 0, 0) {
         double y[ND];
         spmv_node<ND, TT>(A.p, vals, A.ph, a, y);
 #pragma unroll
         for (int i = 0; i < ND; ++i) {
           A.v[ND * a + i] = y[i];
-          l1 += A.r0[ND * a + i] * y[i];
+          lv[0] += A.r0[ND * a + i] * y[i];
         }
-      }
-      publish(0, 0, l1);
+      });
       if (!(ok = grid_barrier(A.bar_count, A.bar_gen, nb))) break;
-      const double r0v = grid_sum(part(0, 0), nb);
+      const double r0v = grid_sum(part(0, 0), NT);
       if (!isfinite(r0v)) { status = 3; break; }
       if (r0v == 0.0) {                         // breakdown: restart from x
         if (restarts >= KRYLOV_MAX_RESTARTS) { status = 2; break; }
@@ -296,40 +333,34 @@ __device__ __forceinline__ void bicgstab_body(const KrylovArgs &A, const int nb,
         for (int i = 0; i < ND; ++i) A.sh[ND * a + i] = sh[i];
       }
       if (!(ok = grid_barrier(A.bar_count, A.bar_gen, nb))) break;
-      double lts = 0.0, ltt = 0.0;
-      LGDM_NODES {
+      LGDM_REDUCE(2, 1, 0) {
         double y[ND];
         spmv_node<ND, TT>(A.p, vals, A.sh, a, y);
 #pragma unroll
         for (int i = 0; i < ND; ++i) {
           A.t[ND * a + i] = y[i];
-          lts += y[i] * A.sv[ND * a + i];
-          ltt += y[i] * y[i];
+          lv[0] += y[i] * A.sv[ND * a + i];
+          lv[1] += y[i] * y[i];
         }
-      }
-      publish(1, 0, lts);
-      publish(1, 1, ltt);
+      });
       if (!(ok = grid_barrier(A.bar_count, A.bar_gen, nb))) break;
-      const double ts = grid_sum(part(1, 0), nb), tt = grid_sum(part(1, 1), nb);
+      const double ts = grid_sum(part(1, 0), NT), tt = grid_sum(part(1, 1), NT);
       omega = (tt > 0.0) ? ts / tt : 0.0;
-      double lrr = 0.0, lrho = 0.0;
-      LGDM_NODES {
+      LGDM_REDUCE(2, 2, 0) {
 #pragma unroll
         for (int i = 0; i < ND; ++i) {
           const int64_t row = ND * a + i;
           A.x[row] += alpha * A.ph[row] + omega * A.sh[row];
           const double rn = A.sv[row] - omega * A.t[row];
           A.r[row] = rn;
-          lrr += rn * rn;
-          lrho += A.r0[row] * rn;
+          lv[0] += rn * rn;
+          lv[1] += A.r0[row] * rn;
         }
-      }
-      publish(2, 0, lrr);
-      publish(2, 1, lrho);
+      });
       if (!(ok = grid_barrier(A.bar_count, A.bar_gen, nb))) break;
-      const double rr = grid_sum(part(2, 0), nb);
+      const double rr = grid_sum(part(2, 0), NT);
       rho_old = rho;
-      rho = grid_sum(part(2, 1), nb);
+      rho = grid_sum(part(2, 1), NT);
       rel = sqrt(rr) / bnorm;
       if (!isfinite(rr)) { status = 3; break; }
       if (rel < best) {
@@ -362,8 +393,7 @@ __device__ __forceinline__ void bicgstab_body(const KrylovArgs &A, const int nb,
     rel = best;
   }
   if (ok && mode != 0 && status != 3) {
-    double ldu = 0.0, lu = 0.0, lde = 0.0, le = 0.0;
-    LGDM_NODES {
+    LGDM_REDUCE(4, 0, 0) {
 #pragma unroll
       for (int i = 0; i < ND; ++i) {
         const int64_t row = ND * a + i;
@@ -371,23 +401,19 @@ __device__ __forceinline__ void bicgstab_body(const KrylovArgs &A, const int nb,
         const double un = A.u[row] + d;
         A.u[row] = un;
         if (i == ND - 1) {
-          lde += d * d;
-          le += un * un;
+          lv[2] += d * d;
+          lv[3] += un * un;
         } else {
-          ldu += d * d;
-          lu += un * un;
+          lv[0] += d * d;
+          lv[1] += un * un;
         }
       }
-    }
-    publish(0, 0, ldu);
-    publish(0, 1, lu);
-    publish(0, 2, lde);
-    publish(0, 3, le);
+    });
     ok = grid_barrier(A.bar_count, A.bar_gen, nb);
     if (ok) {
       double nrm[4];
 #pragma unroll
-      for (int k = 0; k < 4; ++k) nrm[k] = sqrt(grid_sum(part(0, k), nb));
+      for (int k = 0; k < 4; ++k) nrm[k] = sqrt(grid_sum(part(0, k), NT));
       if (bid == 0 && threadIdx.x == 0) {
         const bool cu = nrm[1] > 0.0 ? nrm[0] <= A.newton_tol * nrm[1] : nrm[0] <= 1e-30;
         const bool ce = nrm[3] > 0.0 ? nrm[2] <= A.newton_tol * nrm[3] : nrm[2] <= 1e-30;
@@ -403,6 +429,7 @@ __device__ __forceinline__ void bicgstab_body(const KrylovArgs &A, const int nb,
     }
   }
 #undef LGDM_NODES
+#undef LGDM_REDUCE
   if (!ok) {
     if (threadIdx.x == 0) atomicMax(&A.res->status, 4);
     return;

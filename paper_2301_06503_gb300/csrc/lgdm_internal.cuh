@@ -96,6 +96,9 @@ cudaError_t launch_set_dirichlet(double *u, const int32_t *dof, const double *sc
 cudaError_t launch_commit(int elem, const MeshView &m, const double *u, double *kappa_hist,
                           cudaStream_t s);
 cudaError_t launch_fill(double *p, int64_t n, double v, cudaStream_t s);
+// stored energy (Eq. 1): per-Gauss-point values into psi [nel*ngp], their sum into *out
+cudaError_t launch_energy(int elem, const MeshView &m, const MatConst &mc, const double *u, const double *kh,
+                          double *psi, double *part, double *out, cudaStream_t s);
 // diag[a] = position of node a in its own neighbour list
 cudaError_t launch_diag_pairs(const PatternView &p, int32_t *diag, cudaStream_t s);
 // message for lgdm_last_error(NULL)
@@ -132,10 +135,37 @@ cudaError_t launch_batch_precond(int nd, const BatchSim *sims, const int32_t *me
 
 constexpr int KRYLOV_THREADS = 256;
 
+// Inner products of the Krylov solvers are summed over fixed tiles of nodes
+// (tile = 32 * 2^k nodes, at most KRYLOV_MAX_TILES tiles per system): a warp
+// sums 32 consecutive nodes in a fixed shuffle tree, a tile adds its warp
+// sums in order, and the tile sums are added in tile order.  The tiles
+// depend on the node count only, so the result of a solve does not depend
+// on how many blocks share the system (alone or in a batch).  A block owns
+// a contiguous range of tiles and at most 32 * KRYLOV_MAXW nodes.
+constexpr int KRYLOV_MAXW = 512;
+constexpr int64_t KRYLOV_MAX_TILES = 2048;
+inline int krylov_tile(int64_t nnode) {
+  int t = 32;
+  while ((nnode + t - 1) / t > KRYLOV_MAX_TILES) t *= 2;
+  return t;
+}
+inline int64_t krylov_ntiles(int64_t nnode) {
+  const int t = krylov_tile(nnode);
+  return nnode > 0 ? (nnode + t - 1) / t : 1;
+}
+// fewest blocks that keep every block within 32 * KRYLOV_MAXW nodes (0: too large)
+inline int64_t krylov_min_blocks(int64_t nnode) {
+  const int t = krylov_tile(nnode);
+  const int64_t per = (int64_t)32 * KRYLOV_MAXW / t;
+  if (per < 1) return 0;
+  return (krylov_ntiles(nnode) + per - 1) / per;
+}
+
 struct KrylovArgs {
   int32_t nd, nnode;
   int32_t max_iter;
   int32_t stall_iters;        // stop after this many iterations without a new best residual
+  int32_t tile, ntiles;       // reduction tiles (krylov_tile, krylov_ntiles)
   double rtol, newton_tol;
   PatternView p;
   const void *vals;           // TT [nnz]
@@ -143,7 +173,7 @@ struct KrylovArgs {
   const double *rhs;          // [ndof]
   double *x, *r, *r0, *pv, *v, *sv, *t, *ph, *sh, *xb;   // [ndof] each; xb = best iterate
   double *u;                  // [ndof] state (modes 1 and 2)
-  double *partial;            // [3 slots][4 values][gridDim]
+  double *partial;            // [3 slots][4 values][ntiles]
   unsigned int *bar_count, *bar_gen;
   SolveResult *res;
 };

@@ -62,22 +62,26 @@ extern "C" lgdm_status lgdm_solve_noalloc(int32_t nd, int32_t nnode, const int32
   }
   const int nblocks_max = bicgstab_max_blocks<double>();
   const int64_t ndof = (int64_t)nd * nnode;
-  int nb = (int)std::min<int64_t>((ndof + 2 * KRYLOV_THREADS - 1) / (2 * KRYLOV_THREADS), nblocks_max);
-  if (nb < 1) nb = 1;
+  const int64_t ntiles = krylov_ntiles(nnode);
   // layout inside the static array
   const size_t vec = up256(sizeof(double) * ndof);
-  const size_t need = 9 * vec + up256(sizeof(double) * nnode * nd * nd) + up256(sizeof(double) * 12 * nb) +
+  const size_t need = 9 * vec + up256(sizeof(double) * nnode * nd * nd) + up256(sizeof(double) * 12 * ntiles) +
                       up256(2 * sizeof(unsigned int)) + up256(sizeof(SolveResult)) + up256(sizeof(int32_t) * nnode);
   if (need > NOALLOC_SCRATCH_BYTES)
     return err(LGDM_ERR_OOM, "system needs " + std::to_string(need) + " bytes of scratch; the static array holds " +
                                  std::to_string(NOALLOC_SCRATCH_BYTES));
+  int64_t nb64 = std::min<int64_t>((ndof + 2 * KRYLOV_THREADS - 1) / (2 * KRYLOV_THREADS), ntiles);
+  nb64 = std::min<int64_t>(std::max<int64_t>(nb64, krylov_min_blocks(nnode)), nblocks_max);
+  if (krylov_min_blocks(nnode) < 1 || nb64 < krylov_min_blocks(nnode))
+    return err(LGDM_ERR_INVALID_ARG, "system too large for one Krylov launch");
+  const int nb = (int)std::max<int64_t>(nb64, 1);
   char *c = static_cast<char *>(base);
   double *v[9];
   for (int k = 0; k < 9; ++k, c += vec) v[k] = reinterpret_cast<double *>(c);
   double *minv = reinterpret_cast<double *>(c);
   c += up256(sizeof(double) * nnode * nd * nd);
   double *partial = reinterpret_cast<double *>(c);
-  c += up256(sizeof(double) * 12 * nb);
+  c += up256(sizeof(double) * 12 * ntiles);
   unsigned int *bar = reinterpret_cast<unsigned int *>(c);
   c += up256(2 * sizeof(unsigned int));
   SolveResult *res = reinterpret_cast<SolveResult *>(c);
@@ -97,6 +101,8 @@ extern "C" lgdm_status lgdm_solve_noalloc(int32_t nd, int32_t nnode, const int32
   a.nnode = nnode;
   a.max_iter = max_iter;
   a.stall_iters = std::max(500, max_iter / 4);
+  a.tile = krylov_tile(nnode);
+  a.ntiles = (int32_t)ntiles;
   a.rtol = rtol;
   a.newton_tol = 0.0;
   a.p = p;

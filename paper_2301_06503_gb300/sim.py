@@ -205,6 +205,12 @@ class Sim:
         self._ck(self._lib.lgdm_get_reaction(self.h, C.byref(r)))
         return float(r.value)
 
+    def energy(self) -> float:
+        """Stored energy (Eq. 1) at the current state."""
+        e = C.c_double()
+        self._ck(self._lib.lgdm_get_energy(self.h, C.byref(e)))
+        return float(e.value)
+
     def run(self, loads):
         """Run the given load values in order; returns (reactions, newton_iters)."""
         reac, its = [], []

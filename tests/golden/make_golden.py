@@ -16,16 +16,25 @@ import time
 HERE = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, os.path.dirname(os.path.dirname(HERE)))
 
+import numpy as np                # noqa: E402
+
 import lgdm_inputs as li          # noqa: E402
+from oracle import constitutive as cm  # noqa: E402
 from oracle import newton as nw   # noqa: E402
 
 
 def curve(problem, n_steps):
     t0 = time.time()
     out = nw.run(problem, n_steps=n_steps, energy=True)
+    mat = problem.material
+    D, _ = cm.damage(out["state"].kappa_hist, mat.kappa0, mat.alpha, mat.beta)
+    nz = np.flatnonzero(D > 0.0)
+    # damage at the committed final state, per Gauss point (element-major), stored sparsely:
+    # every Gauss point not listed has D = 0 exactly
     return {"load": out["load"].tolist(), "reaction": out["reaction"].tolist(),
             "newton_iters": out["newton_iters"].tolist(), "psi": out["psi"].tolist(),
-            "dissipated": out["dissipated"].tolist(), "oracle_seconds": time.time() - t0}
+            "dissipated": out["dissipated"].tolist(), "oracle_seconds": time.time() - t0,
+            "damage_final": {"n_gp": int(D.size), "idx": nz.tolist(), "val": D[nz].tolist()}}
 
 
 CASES = {

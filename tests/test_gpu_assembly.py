@@ -131,3 +131,17 @@ def test_single_element_meshes():
         assert abs(K - Kref).max() <= 1e-12 * abs(Kref).max()
         assert np.abs(rhs - rref).max() <= 1e-12 * max(np.abs(rref).max(), 1e-300)
         s.close()
+
+
+@pytest.mark.parametrize("name", ["bar", "plate", "beam"])
+def test_stored_energy_matches_oracle(name):
+    """Integrated free energy (Eq. 1) at a damaged random state, FP64 to 1e-12."""
+    from oracle import newton as on
+    p = _problems()[name]
+    u, kh = li.random_state(p.mesh, seed=11, kappa0=p.material.kappa0)
+    s = _sim(p)
+    s.set_state(u, kh)
+    psi = s.energy()
+    ref = on.free_energy(p, on.State(u, np.maximum(kh, 0.0)))
+    s.close()
+    assert abs(psi - ref) <= 1e-12 * abs(ref), (psi, ref)

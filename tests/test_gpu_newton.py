@@ -170,6 +170,31 @@ def test_bar_curve_fp32_tangent():
 GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
 
 
+# Accuracy of each result against the FP64 oracle (peak load and dissipated
+# energy relative, damage field absolute over all Gauss points): the FP64 path
+# to curve parity, the FP32-tangent path (inexact Newton) to its own targets.
+ACCURACY = {"fp64": {"curve": 1e-6, "peak": 1e-6, "dissipated": 1e-6, "damage": 1e-8},
+            "fp32": {"curve": 1e-6, "peak": 1e-4, "dissipated": 1e-4, "damage": 1e-5}}
+
+
+def _accuracy(p, g, reac, psi, dmg):
+    """Errors of a GPU run against a stored oracle run; dissipated energy is
+    the external work (trapezoid rule over the load-displacement points) minus
+    the stored energy (Eq. 1) at the last committed state."""
+    load = np.concatenate([[0.0], np.asarray(g["load"])])
+    rp = np.concatenate([[0.0], reac])
+    w_ext = float(np.sum(0.5 * (rp[1:] + rp[:-1]) * np.diff(load)))
+    ref = np.asarray(g["reaction"])
+    out = {"curve": np.abs(reac - ref).max() / np.abs(ref).max(),
+           "peak": abs(reac.max() - ref.max()) / abs(ref.max()),
+           "dissipated": abs((w_ext - psi) - g["dissipated"][-1]) / abs(g["dissipated"][-1])}
+    if "damage_final" in g:
+        dref = np.zeros(g["damage_final"]["n_gp"])
+        dref[np.asarray(g["damage_final"]["idx"], dtype=np.int64)] = g["damage_final"]["val"]
+        out["damage"] = np.abs(dmg - dref).max()
+    return out
+
+
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 def test_full_size_plate_prefix_against_oracle(precision):
     """200 x 200 notched plate (the benchmark workload), the oracle's first 30
@@ -182,10 +207,28 @@ def test_full_size_plate_prefix_against_oracle(precision):
     p = li.sen_plate_problem()
     s = _sim(p, precision=precision)
     reac, its = s.run(g["load"])
+    psi, dmg = s.energy(), s.field("damage")
     s.close()
-    ref = np.asarray(g["reaction"])
-    err = np.abs(reac - ref).max() / np.abs(ref).max()
-    assert err <= 1e-6, (err, int(np.argmax(np.abs(reac - ref))))
+    err = _accuracy(p, g, reac, psi, dmg)
+    print(f"\naccuracy {precision} plate 200x200, 30 steps:", {k: f"{v:.2e}" for k, v in err.items()})
+    for k, v in err.items():
+        assert v <= ACCURACY[precision][k], (k, v)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_bar_accuracy_against_stored_oracle(precision):
+    """1D bar, all 200 steps (peak and softening): peak load, dissipated
+    energy and the final damage field against the stored oracle run."""
+    g = json.load(open(os.path.join(GOLDEN, "bar1d.json")))
+    p = li.bar_problem()
+    s = _sim(p, precision=precision)
+    reac, _ = s.run(g["load"])
+    psi, dmg = s.energy(), s.field("damage")
+    s.close()
+    err = _accuracy(p, g, reac, psi, dmg)
+    print(f"\naccuracy {precision} bar, 200 steps:", {k: f"{v:.2e}" for k, v in err.items()})
+    for k, v in err.items():
+        assert v <= ACCURACY[precision][k], (k, v)
 
 
 def test_bar_curve_against_stored_oracle():
