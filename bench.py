@@ -16,9 +16,10 @@ pinned host buffers (state in, damage field and reaction out).
 
 Other workloads (--workload): bar (100 two-node elements), beam (200 x 40 x
 40 hexahedra, 1.35M dofs), batch (256 notched plates of 20..300 elements per
-edge in one batch: persistent element kernel, grouped solves, a CUDA graph
-per Newton step, autotuned tiles; a step solves load increment 1 of all of
-them).  --precision fp32 assembles the tangent and applies the
+edge in one batch, 4.84M elements: persistent element kernel, grouped
+solves, autotuned tiles; a step is one batched Newton iteration of all of
+them at load increment 1 -- assembly, solve, update -- and the phase timers
+run the batch without its CUDA graph).  --precision fp32 assembles the tangent and applies the
 preconditioner in FP32 (residual, inner products and tests in FP64).
 
 --serving runs the request-serving comparison instead and prints its own
@@ -58,12 +59,14 @@ def parse():
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
     ap.add_argument("--workload", default="plate", choices=["plate", "bar", "beam", "batch"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", default="loadstep", choices=["loadstep", "newton"],
-                    help="loadstep: a step is a converged load increment; newton: one Newton iteration "
-                         "(assemble + solve + update), used for profiling captures")
+    ap.add_argument("--mode", default=None, choices=["loadstep", "newton"],
+                    help="loadstep: a step is a converged load increment (default for one simulation); "
+                         "newton: one Newton iteration, assemble + solve + update (default for the batch)")
+    ap.add_argument("--batch-count", type=int, default=256,
+                    help="simulations of the batch workload (the first ones of the seeded 256-plate draw)")
     ap.add_argument("--serving", action="store_true")
     ap.add_argument("--requests", type=int, default=16)
-    ap.add_argument("--serve-steps", type=int, default=300)
+    ap.add_argument("--serve-steps", type=int, default=10)
     ap.add_argument("--budget-gb", type=float, default=64.0)
     ap.add_argument("--max-resident", type=int, default=64)
     ap.add_argument("--max-krylov", type=int, default=5000,
@@ -79,7 +82,7 @@ def workload(name):
         return [li.bar_problem()], "bar_l2_100"
     if name == "beam":
         return [li.tpb_beam_problem()], "tpb_beam_h8_200x40x40"
-    return li.batch_plate_problems(), "batch_256_plates_q4_20to300"
+    return li.batch_plate_problems(), "batch_plates_q4_20to300"
 
 
 def dist_env():
@@ -404,6 +407,9 @@ def run_ours(args):
         torch.distributed.barrier()
     build()
     probs, label = workload(args.workload)
+    if args.workload == "batch":
+        probs = probs[:args.batch_count]
+        label = f"batch_{len(probs)}_plates_q4_20to300"
     leg = BatchLeg(probs, label, args) if args.workload == "batch" else SingleLeg(probs[0], label, args)
     stream = leg.stream
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
@@ -569,6 +575,8 @@ def run_serving(args):
 
 def main():
     args = parse()
+    if args.mode is None:
+        args.mode = "newton" if args.workload == "batch" else "loadstep"
     if args.serving:
         run_serving(args)
         return

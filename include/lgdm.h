@@ -185,7 +185,15 @@ lgdm_status lgdm_update(lgdm_sim *sim, int32_t *converged);
 /* One Newton iteration: assemble, solve (BiCGSTAB; when it does not reach
  * krylov_rtol, restarted GMRES continues from its best iterate), then the
  * update and the convergence test.  The increment is accepted as converged
- * only if its linear solve reached a relative residual of 1e-3 or less. */
+ * only if its linear solve reached a relative residual of 1e-3 or less.
+ * When the solve with the consistent tangent (Eq. 11a-d) ends above that
+ * bound, the system is assembled again with the secant tangent (the loading
+ * indicator chi taken as 0, which drops the D'(kappa) terms of Eq. 11b and
+ * 11d; residual and damage unchanged) and solved; the load step continues
+ * with the secant tangent (a quasi-Newton iteration on the same residual,
+ * so the converged state is the same).  The next load step starts with the
+ * consistent tangent again, unless the previous steps all needed the
+ * secant one (then every 8th step tries the consistent tangent). */
 lgdm_status lgdm_newton_step(lgdm_sim *sim, int32_t *converged, int32_t *krylov_iters);
 
 /* One load step to `load`: begin_step, Newton iterations until convergence,
@@ -218,7 +226,8 @@ lgdm_status lgdm_reset_timers(lgdm_sim *sim);
 
 /* Counters since creation: [0] kernel launches, [1] assemblies,
  * [2] Krylov iterations, [3] Newton iterations, [4] committed load steps,
- * [5] increment halvings.  n entries are written (n <= 6). */
+ * [5] increment halvings, [6] Newton iterations taken with the secant
+ * tangent (see lgdm_newton_step).  n entries are written (n <= 7). */
 lgdm_status lgdm_get_counters(const lgdm_sim *sim, int64_t *counters, int32_t n);
 
 /* Stored energy Psi (Eq. 1) integrated over the mesh at the current state,
@@ -264,12 +273,12 @@ lgdm_status lgdm_batch_autotune(lgdm_batch *batch, int32_t *block_threads, int32
 /* Batched assembly of the members with active[i] != 0 (host array of n). */
 lgdm_status lgdm_batch_assemble(lgdm_batch *batch, const int32_t *active);
 /* Phase timers of a batch: CUDA events on the batch stream around the
- * element launches, the gathers, the preconditioner set-ups and the first
- * (mode 0) grouped solve of every Newton step, in that order (also inside a
- * captured graph; turning timers on or off drops the graph so that the next
- * step captures it again).  get_timers returns the summed milliseconds and
- * the number of timed steps per phase {element, gather, precond, krylov};
- * reset != 0 zeroes them. */
+ * element launches, the gathers, the preconditioner set-ups and the grouped
+ * solve of every batched assembly-and-solve pass, in that order.  While
+ * timers are on the passes are launched directly, not through the captured
+ * graph.  get_timers returns the summed milliseconds and the number of timed
+ * passes per phase {element, gather, precond, krylov}; reset != 0 zeroes
+ * them. */
 lgdm_status lgdm_batch_enable_timers(lgdm_batch *batch, int32_t on);
 lgdm_status lgdm_batch_get_timers(lgdm_batch *batch, double *ms4, int64_t *count4, int32_t reset);
 

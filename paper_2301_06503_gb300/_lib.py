@@ -15,7 +15,8 @@ PRECOND_JACOBI, PRECOND_NODE_BLOCK = 0, 1
 FIELD_U, FIELD_KAPPA_HIST, FIELD_DAMAGE, FIELD_DELTA, FIELD_RESIDUAL, FIELD_RHS = range(6)
 NPHASES = 6
 PHASES = ("element", "gather", "precond", "krylov", "commit", "begin_step")
-COUNTERS = ("kernel_launches", "assemblies", "krylov_iters", "newton_iters", "load_steps", "halvings")
+COUNTERS = ("kernel_launches", "assemblies", "krylov_iters", "newton_iters", "load_steps", "halvings",
+            "secant_iters")
 STATUS = {0: "ok", 1: "invalid argument", 2: "workspace too small", 3: "CUDA error",
           4: "Newton did not converge", 5: "non-finite value", 6: "device wait timed out",
           7: "call out of order"}

@@ -173,7 +173,12 @@ struct lgdm_sim {
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_pending;
   double phase_ms[LGDM_NPHASES] = {};
   int64_t phase_n[LGDM_NPHASES] = {};
-  int64_t counters[6] = {};
+  int64_t counters[7] = {};
+  // secant-tangent fallback: current mode, the value last written to the
+  // device descriptor, whether this load step used it, consecutive steps
+  int secant = 0, secant_dev = 0;
+  bool step_secant = false;
+  int secant_streak = 0;
   // host copies
   std::vector<int32_t> h_nbr_ptr, h_nbr;
   std::string err;
@@ -640,6 +645,9 @@ lgdm_status lgdm_set_state(lgdm_sim *s, const double *u, const double *kh) {
                                  s->stream));
   LGDM_CUDA(s, cudaStreamSynchronize(s->stream));
   s->assembled = false;
+  s->secant = 0;
+  s->secant_streak = 0;
+  s->step_secant = false;
   return LGDM_OK;
 }
 
@@ -652,6 +660,9 @@ lgdm_status lgdm_reset_state(lgdm_sim *s) {
   s->counters[0] += 1;
   s->load_commit = 0.0;
   s->assembled = false;
+  s->secant = 0;
+  s->secant_streak = 0;
+  s->step_secant = false;
   return LGDM_OK;
 }
 
@@ -682,6 +693,10 @@ lgdm_status lgdm_get_field(lgdm_sim *s, int32_t which, double *dst, size_t n) {
 lgdm_status lgdm_begin_step(lgdm_sim *s, double load) {
   if (!s) return fail(nullptr, LGDM_ERR_INVALID_ARG, "NULL handle");
   PhaseTimer pt(s, 5);
+  // a load step starts with the consistent tangent, unless the previous
+  // steps needed the secant one (then every 8th step tries it again)
+  s->secant = (s->secant_streak > 0 && s->secant_streak % 8 != 0) ? 1 : 0;
+  s->step_secant = false;
   LGDM_CUDA(s, cudaMemcpyAsync(s->u, s->u_commit, sizeof(double) * s->ndof, cudaMemcpyDeviceToDevice, s->stream));
   LGDM_CUDA(s, launch_set_dirichlet(s->u, s->dir_dof, s->dir_scale, s->ndir, load, s->stream));
   s->counters[0] += 1;
@@ -691,6 +706,11 @@ lgdm_status lgdm_begin_step(lgdm_sim *s, double load) {
 
 lgdm_status lgdm_assemble(lgdm_sim *s) {
   if (!s) return fail(nullptr, LGDM_ERR_INVALID_ARG, "NULL handle");
+  if (s->secant != s->secant_dev) {            // the tangent mode lives in the device descriptor
+    s->secant_dev = s->secant;
+    char *dst = reinterpret_cast<char *>(s->d_self) + offsetof(BatchSim, mc) + offsetof(MatConst, secant);
+    LGDM_CUDA(s, cudaMemcpyAsync(dst, &s->secant_dev, sizeof(int32_t), cudaMemcpyHostToDevice, s->stream));
+  }
   const MeshView mv = s->mesh_view();
   const PatternView pv = s->pattern_view();
   const int32_t *mem = s->d_one, *act = s->d_one + 1;
@@ -855,17 +875,29 @@ lgdm_status run_gmres(lgdm_sim *s, SolveResult *out) {
   return finish_launch(s, 0, out);
 }
 
+// A solve whose increment Newton may use.
+bool solve_acceptable(lgdm_status st, const SolveResult &r) {
+  return st == LGDM_OK && (r.status == 0 || r.rel_res <= KRYLOV_NEWTON_ETA);
+}
+
+// GMRES continues a BiCGSTAB solve that ended far from krylov_rtol -- unless
+// the result is not even usable and the secant tangent is still to be tried
+// (with_secant_left): a new tangent is then the better next step.
+bool wants_gmres(const lgdm_sim *s, lgdm_status st, const SolveResult &r, bool with_secant_left) {
+  const bool short_of = (st == LGDM_ERR_NONFINITE) || (r.status != 0 && r.rel_res > 1e3 * s->opt.krylov_rtol);
+  if (!short_of || s->opt.gmres_m <= 0) return false;
+  return !(with_secant_left && !solve_acceptable(st, r));
+}
+
 // Solve with BiCGSTAB, continue with GMRES when it falls short of krylov_rtol.
-lgdm_status solve_robust(lgdm_sim *s, SolveResult *out) {
+lgdm_status solve_robust(lgdm_sim *s, SolveResult *out, bool with_secant_left = false) {
   if (s->opt.krylov_method == 1) {
     LGDM_CUDA(s, cudaMemsetAsync(s->kv[0], 0, sizeof(double) * s->ndof, s->stream));
     return run_gmres(s, out);
   }
   lgdm_status st = run_krylov(s, 0, out);
   if (st != LGDM_OK && st != LGDM_ERR_NONFINITE) return st;
-  // hand over to GMRES only when BiCGSTAB ended far from its tolerance
-  const bool short_of = (st == LGDM_ERR_NONFINITE) || (out->status != 0 && out->rel_res > 1e3 * s->opt.krylov_rtol);
-  if (!short_of || s->opt.gmres_m <= 0) return st;
+  if (!wants_gmres(s, st, *out, with_secant_left)) return st;
   const int32_t bicg_iters = out->iters;
   if (st == LGDM_ERR_NONFINITE)
     LGDM_CUDA(s, cudaMemsetAsync(s->kv[0], 0, sizeof(double) * s->ndof, s->stream));
@@ -905,9 +937,23 @@ lgdm_status lgdm_newton_step(lgdm_sim *s, int32_t *converged, int32_t *krylov_it
   lgdm_status st = lgdm_assemble(s);
   if (st != LGDM_OK) return st;
   SolveResult r{};
-  st = solve_robust(s, &r);
+  st = solve_robust(s, &r, !s->secant);
+  int32_t its = r.iters;
+  if (!solve_acceptable(st, r) && !s->secant && (st == LGDM_OK || st == LGDM_ERR_NONFINITE)) {
+    // the consistent tangent defeated the Krylov solver: secant tangent for
+    // the rest of this load step
+    s->secant = 1;
+    st = lgdm_assemble(s);
+    if (st != LGDM_OK) return st;
+    st = solve_robust(s, &r);
+    its += r.iters;
+    s->last.iters = its;
+  }
   if (st != LGDM_OK) return st;
-  const int32_t its = r.iters;
+  if (s->secant) {
+    s->step_secant = true;
+    s->counters[6] += 1;
+  }
   SolveResult u{};
   st = run_krylov(s, 2, &u);
   s->assembled = false;
@@ -921,6 +967,8 @@ lgdm_status lgdm_commit(lgdm_sim *s) {
   PhaseTimer pt(s, 4);
   s->counters[0] += (s->n_reac > 0) ? 3 : 1;
   s->counters[4] += 1;
+  s->secant_streak = s->step_secant ? s->secant_streak + 1 : 0;
+  s->step_secant = false;
   LGDM_CUDA(s, launch_commit(s->elem, s->mesh_view(), s->u, s->kappa_hist, s->stream));
   LGDM_CUDA(s, cudaMemcpyAsync(s->u_commit, s->u, sizeof(double) * s->ndof, cudaMemcpyDeviceToDevice, s->stream));
   if (s->n_reac > 0) {
@@ -977,7 +1025,7 @@ lgdm_status lgdm_reset_timers(lgdm_sim *s) {
 }
 
 lgdm_status lgdm_get_counters(const lgdm_sim *s, int64_t *c, int32_t n) {
-  if (!s || !c || n < 0 || n > 6) return fail(nullptr, LGDM_ERR_INVALID_ARG, "bad counters request");
+  if (!s || !c || n < 0 || n > 7) return fail(nullptr, LGDM_ERR_INVALID_ARG, "bad counters request");
   for (int k = 0; k < n; ++k) c[k] = s->counters[k];
   return LGDM_OK;
 }
@@ -1099,6 +1147,7 @@ struct lgdm_batch {
   std::string graph_note;
   cudaGraphExec_t graph = nullptr;
   std::vector<int32_t> h_active;
+  std::vector<int32_t> h_secant;       // tangent mode written into each member's descriptor
   std::vector<SolveResult> h_res;
   std::string err;
   // phase timers: events before the element launches, after them, after the
@@ -1226,14 +1275,17 @@ bool batch_capture(lgdm_batch *b, bool with_solve) {
 }
 
 lgdm_status batch_assemble_and_solve(lgdm_batch *b) {
-  // the first step runs directly (kernel attributes get set outside any capture)
-  if (b->graph_on && !b->graph_tried && b->direct_issues > 0) {
+  // the first step runs directly (kernel attributes get set outside any
+  // capture); with phase timers on every step runs directly (events recorded
+  // by graph nodes give no elapsed times)
+  const bool use_graph = b->graph_on && !b->timers_on;
+  if (use_graph && !b->graph_tried && b->direct_issues > 0) {
     b->graph_tried = true;
     if (batch_capture(b, true)) b->graph_mode = 2;
     else if (batch_capture(b, false)) b->graph_mode = 1;
     b->graph_ok = b->graph_mode > 0;
   }
-  if (b->graph_on && b->graph_ok) {
+  if (use_graph && b->graph_ok) {
     LGDM_BCUDA(b, cudaGraphLaunch(b->graph, b->stream));
     if (b->graph_mode == 1) return batch_issue_solve(b, 0);
     return LGDM_OK;
@@ -1392,6 +1444,7 @@ lgdm_status lgdm_batch_create(lgdm_sim *const *sims, int32_t n, void *ws, size_t
     LGDM_BCUDA(b, cudaMemcpyAsync(b->d_sims, hs.data(), sizeof(BatchSim) * n, cudaMemcpyHostToDevice, b->stream));
     LGDM_BCUDA(b, cudaMemcpyAsync(b->d_kargs, hk.data(), sizeof(KrylovArgs) * n, cudaMemcpyHostToDevice, b->stream));
     b->h_active.assign(n, 0);
+    b->h_secant.assign(n, 0);
     b->h_res.resize(n);
     // tile prefixes for the default block size
     for (auto &g : b->groups) {
@@ -1452,7 +1505,7 @@ lgdm_status lgdm_batch_enable_timers(lgdm_batch *b, int32_t on) {
   if (on)
     for (auto &e : b->tev)
       if (!e) LGDM_BCUDA(b, cudaEventCreate(&e));
-  if ((on != 0) != b->timers_on) {               // the graph holds the event records or not: capture again
+  if ((on != 0) != b->timers_on) {               // capture the graph again after a change
     if (b->graph) cudaGraphExecDestroy(b->graph);
     b->graph = nullptr;
     b->graph_ok = b->graph_tried = false;
@@ -1476,14 +1529,19 @@ lgdm_status lgdm_batch_get_timers(lgdm_batch *b, double *ms, int64_t *count, int
   return LGDM_OK;
 }
 
-lgdm_status lgdm_batch_newton_step(lgdm_batch *b, const int32_t *active, int32_t *converged, int32_t *krylov_iters) {
-  if (!b || !active) return bfail(b, LGDM_ERR_INVALID_ARG, "NULL argument");
-  int nact = 0;
+// One batched assembly and solve of the members flagged in b->h_active,
+// each with its own tangent mode; members the first solve left far from
+// its tolerance continue with GMRES, one by one.  kit accumulates the Krylov
+// iterations, res receives each member's final solve.
+lgdm_status batch_solve_pass(lgdm_batch *b, std::vector<int32_t> &kit, std::vector<SolveResult> &res,
+                             std::vector<lgdm_status> &mst) {
   for (int i = 0; i < b->n; ++i) {
-    b->h_active[i] = active[i] ? 1 : 0;
-    nact += b->h_active[i];
+    lgdm_sim *s = b->sims[i];
+    if (!b->h_active[i] || b->h_secant[i] == s->secant) continue;
+    b->h_secant[i] = s->secant;                       // the tangent mode lives in the batch descriptor
+    char *dst = reinterpret_cast<char *>(b->d_sims + i) + offsetof(BatchSim, mc) + offsetof(MatConst, secant);
+    LGDM_BCUDA(b, cudaMemcpyAsync(dst, &b->h_secant[i], sizeof(int32_t), cudaMemcpyHostToDevice, b->stream));
   }
-  if (nact == 0) return LGDM_OK;
   LGDM_BCUDA(b, cudaMemcpyAsync(b->d_active, b->h_active.data(), sizeof(int32_t) * b->n, cudaMemcpyHostToDevice, b->stream));
   lgdm_status st = batch_assemble_and_solve(b);
   if (st != LGDM_OK) return st;
@@ -1491,31 +1549,79 @@ lgdm_status lgdm_batch_newton_step(lgdm_batch *b, const int32_t *active, int32_t
   LGDM_BCUDA(b, cudaMemcpyAsync(b->h_res.data(), b->d_res, sizeof(SolveResult) * b->n, cudaMemcpyDeviceToHost, b->stream));
   LGDM_BCUDA(b, cudaStreamSynchronize(b->stream));
   batch_resolve_timers(b);
-  // members the first solve left far from its tolerance: GMRES, one by one
   for (int i = 0; i < b->n; ++i) {
     if (!b->h_active[i]) continue;
     lgdm_sim *s = b->sims[i];
-    SolveResult &r = b->h_res[i];
+    SolveResult r = b->h_res[i];
     s->counters[0] += 4;
     s->counters[1] += 1;
     s->counters[2] += r.iters;
     s->last = r;
     if (r.status == 4) return bfail(b, LGDM_ERR_TIMEOUT, "grid barrier timed out in a grouped Krylov launch");
     const bool nonfinite = r.status == 3;
-    if ((nonfinite || (r.status != 0 && r.rel_res > 1e3 * s->opt.krylov_rtol)) && s->opt.gmres_m > 0) {
+    lgdm_status ms = nonfinite ? LGDM_ERR_NONFINITE : LGDM_OK;
+    if (wants_gmres(s, ms, r, !s->secant)) {
       if (nonfinite)
         LGDM_BCUDA(b, cudaMemsetAsync(s->kv[0], 0, sizeof(double) * s->ndof, s->stream));
       else
         LGDM_BCUDA(b, cudaMemcpyAsync(s->kv[0], s->kv[9], sizeof(double) * s->ndof, cudaMemcpyDeviceToDevice, s->stream));
       SolveResult g{};
       const int32_t bi = r.iters;
-      st = run_gmres(s, &g);
-      if (st != LGDM_OK && st != LGDM_ERR_NONFINITE) return bfail(b, st, s->err);
+      ms = run_gmres(s, &g);
+      if (ms != LGDM_OK && ms != LGDM_ERR_NONFINITE) return bfail(b, ms, s->err);
       g.iters += bi;
       s->last.iters = g.iters;
       r = g;
     }
-    if (krylov_iters) krylov_iters[i] = r.iters;
+    kit[i] += r.iters;
+    res[i] = r;
+    mst[i] = ms;
+  }
+  return LGDM_OK;
+}
+
+lgdm_status lgdm_batch_newton_step(lgdm_batch *b, const int32_t *active, int32_t *converged, int32_t *krylov_iters) {
+  if (!b || !active) return bfail(b, LGDM_ERR_INVALID_ARG, "NULL argument");
+  int nact = 0;
+  std::vector<int32_t> act(b->n);
+  for (int i = 0; i < b->n; ++i) {
+    act[i] = active[i] ? 1 : 0;
+    nact += act[i];
+  }
+  if (nact == 0) return LGDM_OK;
+  std::vector<int32_t> kit(b->n, 0);
+  std::vector<SolveResult> res(b->n);
+  std::vector<lgdm_status> mst(b->n, LGDM_OK);
+  b->h_active = act;
+  lgdm_status st = batch_solve_pass(b, kit, res, mst);
+  if (st != LGDM_OK) return st;
+  // members whose consistent tangent defeated the Krylov solver: again with
+  // the secant tangent, for the rest of their load step
+  int nretry = 0;
+  for (int i = 0; i < b->n; ++i) {
+    lgdm_sim *s = b->sims[i];
+    const bool retry = act[i] && !s->secant && !solve_acceptable(mst[i], res[i]);
+    b->h_active[i] = retry ? 1 : 0;
+    if (retry) {
+      s->secant = 1;
+      ++nretry;
+    }
+  }
+  if (nretry > 0) {
+    st = batch_solve_pass(b, kit, res, mst);
+    if (st != LGDM_OK) return st;
+  }
+  b->h_active = act;
+  LGDM_BCUDA(b, cudaMemcpyAsync(b->d_active, b->h_active.data(), sizeof(int32_t) * b->n, cudaMemcpyHostToDevice, b->stream));
+  for (int i = 0; i < b->n; ++i) {
+    if (!act[i]) continue;
+    lgdm_sim *s = b->sims[i];
+    s->last.iters = kit[i];
+    if (krylov_iters) krylov_iters[i] = kit[i];
+    if (s->secant) {
+      s->step_secant = true;
+      s->counters[6] += 1;
+    }
   }
   // batched update and Newton test (mode 2), same block groups
   st = batch_issue_solve(b, 2);

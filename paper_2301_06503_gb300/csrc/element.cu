@@ -47,6 +47,7 @@ MatConst make_matconst(const lgdm_material &m, int dim) {
   c.eta = m.eta;
   c.h = m.h;
   c.c = m.c;
+  c.secant = 0;
   return c;
 }
 
@@ -263,8 +264,9 @@ __device__ __forceinline__ void element_tile(const MeshView &m, const MatConst &
     const double eq = equivalent_strain<DIM>(mc, eps, deq);
     // trial history (Eq. A.2) and damage (Eq. A.1)
     const double khq = kh[(int64_t)e * NGP + q];
-    const bool chi = eb > khq;
-    const double kap = chi ? eb : khq;
+    const bool up = eb > khq;                                    // loading (Eq. A.2)
+    const double kap = up ? eb : khq;
+    const bool chi = up && !mc.secant;
     double D = 0.0, dD = 0.0;
     if (kap > mc.kappa0) {
       const double ex = exp(-mc.beta * (kap - mc.kappa0));

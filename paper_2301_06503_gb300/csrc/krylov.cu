@@ -23,9 +23,6 @@ namespace lgdm {
 constexpr int KT = KRYLOV_THREADS;
 constexpr unsigned long long BARRIER_NS = 2000000000ull;   // 2 s
 constexpr int KRYLOV_MAX_RESTARTS = 8;
-// Largest relative linear residual with which a Newton increment may still be
-// accepted as the converged one (an inexact-Newton forcing term).
-constexpr double KRYLOV_NEWTON_ETA = 1e-3;
 
 __device__ __forceinline__ unsigned long long globaltimer() {
   unsigned long long t;

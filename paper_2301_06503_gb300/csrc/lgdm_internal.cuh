@@ -45,9 +45,18 @@ struct MatConst {
   double kappa0, alpha, beta;            // Eq. A.1
   double g_a, g_b, eta;                  // g = g_a e^{-eta D} + g_b  (Eq. A.4)
   double h, c;
+  // 1: assemble the secant tangent -- the loading indicator chi of Eq. 11b
+  // and 11d is taken as 0, which drops the D'(kappa) terms; the residual
+  // and the damage are unchanged
+  int32_t secant;
 };
 
 MatConst make_matconst(const lgdm_material &m, int dim);
+
+// Largest relative linear residual with which a Newton increment may still be
+// accepted (an inexact-Newton forcing term); a solve that ends above it with
+// the consistent tangent is repeated with the secant tangent.
+constexpr double KRYLOV_NEWTON_ETA = 1e-3;
 
 // ---------------------------------------------------------------- device views
 struct MeshView {

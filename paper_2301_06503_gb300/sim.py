@@ -196,8 +196,8 @@ class Sim:
         return {name: (float(ms[k]), int(n[k])) for k, name in enumerate(L.PHASES)}
 
     def counters(self):
-        c = np.zeros(6, np.int64)
-        self._ck(self._lib.lgdm_get_counters(self.h, _p(c, C.c_int64), 6))
+        c = np.zeros(len(L.COUNTERS), np.int64)
+        self._ck(self._lib.lgdm_get_counters(self.h, _p(c, C.c_int64), len(L.COUNTERS)))
         return {name: int(c[k]) for k, name in enumerate(L.COUNTERS)}
 
     def reaction(self) -> float:

@@ -6,7 +6,10 @@ from the CUDA path).  Run from the repository root:
     python tests/golden/make_golden.py [name ...]
 
 names: bar1d (1D bar, all 200 steps), sen_plate_prefix (200 x 200 notched
-plate, first 30 load steps, ~30 CPU minutes).
+plate, first 30 load steps, ~30 CPU minutes), batch_plate8_step1 (plate 8 of
+the 256-plate batch, 200 x 200, first load step: its Newton iterations pass
+through tangents that defeat the Jacobi-preconditioned Krylov solvers,
+~1 CPU minute).
 """
 import json
 import os
@@ -40,6 +43,7 @@ def curve(problem, n_steps):
 CASES = {
     "bar1d": lambda: ("bar_problem()", li.bar_problem(), 200),
     "sen_plate_prefix": lambda: ("sen_plate_problem()", li.sen_plate_problem(), 30),
+    "batch_plate8_step1": lambda: ("batch_plate_problems()[8]", li.batch_plate_problems()[8], 1),
 }
 
 

@@ -173,7 +173,11 @@ GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
 # Accuracy of each result against the FP64 oracle (peak load and dissipated
 # energy relative, damage field absolute over all Gauss points): the FP64 path
 # to curve parity, the FP32-tangent path (inexact Newton) to its own targets.
-ACCURACY = {"fp64": {"curve": 1e-6, "peak": 1e-6, "dissipated": 1e-6, "damage": 1e-8},
+# Both sides stop Newton at increments of 1e-8 relative, so a converged
+# micro-strain field carries errors of that order, and the damage slope
+# dD/dkappa (up to ~1e4 here) turns them into damage differences of ~1e-8:
+# the FP64 damage bound is 1e-7.
+ACCURACY = {"fp64": {"curve": 1e-6, "peak": 1e-6, "dissipated": 1e-6, "damage": 1e-7},
             "fp32": {"curve": 1e-6, "peak": 1e-4, "dissipated": 1e-4, "damage": 1e-5}}
 
 
@@ -239,3 +243,38 @@ def test_bar_curve_against_stored_oracle():
     s.close()
     ref = np.asarray(g["reaction"])
     assert np.abs(reac - ref).max() <= 1e-6 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_secant_fallback_hard_member_against_oracle(precision):
+    """Plate 8 of the 256-plate batch (200 x 200), first load step: from the
+    fourth Newton iteration on, the consistent tangent defeats the
+    Jacobi-preconditioned BiCGSTAB and GMRES; the step continues with the
+    secant tangent and must reach the oracle's converged state (the oracle
+    solves every tangent directly), alone and inside a batch, bitwise."""
+    from paper_2301_06503_gb300 import Batch, Sim
+    g = json.load(open(os.path.join(GOLDEN, "batch_plate8_step1.json")))
+    p = li.batch_plate_problems()[8]
+    st = torch.cuda.Stream()
+    s = Sim(p.mesh, p.material, p.bcs, stream=st, precision=precision)
+    reac, its = s.run(g["load"])
+    psi, dmg = s.energy(), s.field("damage")
+    c = s.counters()
+    s.close()
+    assert c["secant_iters"] > 0                     # the fallback was taken
+    err = _accuracy(p, g, reac, psi, dmg)
+    print(f"\nsecant fallback {precision} plate 8: newton {int(its[0])} secant {c['secant_iters']}",
+          {k: f"{v:.2e}" for k, v in err.items()})
+    for k in ("curve", "peak", "damage"):            # one step: no dissipation to speak of yet
+        assert err[k] <= ACCURACY[precision][k], (k, err[k])
+    # the same member inside a batch with two small plates: bitwise equal
+    small = [li.sen_plate_problem(10, 10, n_steps=300, material=p.material),
+             li.sen_plate_problem(16, 16, n_steps=300)]
+    sims = [Sim(q.mesh, q.material, q.bcs, stream=st, precision=precision) for q in [p] + small]
+    b = Batch(sims)
+    b.run_step([q.load(1) for q in [p] + small])
+    r_batch = sims[0].reaction()
+    b.close()
+    for x in sims:
+        x.close()
+    assert r_batch == reac[0]
