@@ -5,11 +5,12 @@
  * points, deterministic assembly into a fixed CSR pattern, a preconditioned
  * Krylov solve, the Newton update and the history commit.
  *
- * The calls follow the paper's statement of the problem (Algorithm 1 and 2:
- * "Input: geometry, material properties, loads and boundary conditions;
- * output: damage and structural response"): a mesh, a material and a set of
- * displacement-controlled Dirichlet conditions go in; load-step, Newton-step,
- * assemble, solve and commit calls drive the incremental-iterative procedure.
+ * The calls follow the paper's statement of the problem (Algorithm 1 and 2
+ * take the geometry, the material, the loads and the boundary conditions and
+ * return the damage field and the structural response): a mesh, a material
+ * and a set of displacement-controlled Dirichlet conditions go in; load-step,
+ * Newton-step, assemble, solve and commit calls drive the
+ * incremental-iterative procedure.
  *
  * Conventions used by every call
  *   - Units: mm, N, MPa.  Scalars are double unless stated.
@@ -54,9 +55,11 @@ typedef enum {
 typedef enum { LGDM_L2 = 1, LGDM_Q4 = 2, LGDM_H8 = 3 } lgdm_elem;
 
 /* Arithmetic of the tangent.  FP64: everything in double.  FP32_TANGENT: the
- * element tangent, the CSR values, the SpMV and the preconditioner in float
- * (an inexact-Newton matrix); residual, Krylov vectors, inner products, the
- * update and the convergence test stay double. */
+ * element tangent is computed in float and the CSR values and node-block
+ * inverses are stored in float (an inexact-Newton matrix); the SpMV and the
+ * preconditioner multiply those floats into double accumulators, and the
+ * residual, Krylov vectors, inner products, the update and the convergence
+ * test stay double. */
 typedef enum { LGDM_PREC_FP64 = 0, LGDM_PREC_FP32_TANGENT = 1 } lgdm_precision;
 
 typedef enum { LGDM_PRECOND_JACOBI = 0, LGDM_PRECOND_NODE_BLOCK = 1 } lgdm_precond;
