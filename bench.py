@@ -166,6 +166,20 @@ def csrc_sha():
     return h.hexdigest()[:16]
 
 
+def job_totals(t_s, units, world, device):
+    """Whole-job time and work over the replicas: the slowest rank's timed
+    seconds and the sum of every rank's units (Gauss points)."""
+    if world <= 1:
+        return t_s, float(units)
+    import torch
+    import torch.distributed as dist
+    tt = torch.tensor([t_s, float(units)], device=device, dtype=torch.float64)
+    tmax = tt.clone()
+    dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+    dist.all_reduce(tt, op=dist.ReduceOp.SUM)
+    return float(tmax[0]), float(tt[1])
+
+
 def _cores_used(cpu_s, wall_s):
     """Threads the oracle actually kept busy: process CPU time over wall time."""
     return max(1, int(round(cpu_s / wall_s))) if wall_s > 0 else 1
@@ -441,15 +455,7 @@ def run_ours(args):
     step_ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
     st = leg.stop_timing()
     t_s = sum(step_ms) / 1e3
-    if world > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([t_s, float(st["gp"])], device="cuda", dtype=torch.float64)
-        tmax = tt.clone()
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-        dist.all_reduce(tt, op=dist.ReduceOp.SUM)
-        t_job, gp_job = float(tmax[0]), float(tt[1])
-    else:
-        t_job, gp_job = t_s, float(st["gp"])
+    t_job, gp_job = job_totals(t_s, st["gp"], world, "cuda")
     value = gp_job / t_job
 
     # ------------------------------------------------ roofline of the dominant kernel

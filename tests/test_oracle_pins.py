@@ -384,3 +384,46 @@ def test_p13_tangent_structure(mi):
     b2 = _blocks(mesh, K2.toarray())
     assert np.abs(b2["ue"]).max() == 0.0
     assert np.abs(b2["ee"] - b2["ee"].T).max() <= 1e-14 * np.abs(b2["ee"]).max()
+
+
+def test_secant_tangent_same_residual_and_root():
+    """The secant tangent (loading indicator chi = 0, i.e. the D'(kappa) terms
+    of Eq. 11b and 11d dropped) changes the Jacobian only: with the history
+    raised to the trial value max(kappa_hist, ebar) chi vanishes while kappa,
+    D and therefore the residual stay the same.  Iterating with it converges
+    (linearly) to the root exact Newton finds, here on a notched plate in its
+    first, damaging load step."""
+    p = li.sen_plate_problem(12, 12, n_steps=100)
+    m, mat = p.mesh, p.material
+    st = nw.initial_state(p)
+    u0 = st.u.copy()
+    u0[p.bcs.dir_dof] = p.bcs.dir_scale * p.load(1)
+    isd = (np.arange(m.ndof) % m.nd) == m.dim
+
+    def system(u, secant):
+        kh = np.maximum(st.kappa_hist, el.gp_ebar(m, u).ravel()) if secant else st.kappa_hist
+        K, r = asm.assemble(m, mat, u, kh)
+        return asm.apply_dirichlet(K, r, p.bcs.dir_dof), r
+
+    def solve(secant):
+        import scipy.sparse.linalg as spla
+        u = u0.copy()
+        for k in range(40):
+            (Kb, rb), _ = system(u, secant)
+            du = spla.spsolve(Kb.tocsc(), -rb)
+            u += du
+            if (np.linalg.norm(du[~isd]) <= 1e-12 * np.linalg.norm(u[~isd])
+                    and np.linalg.norm(du[isd]) <= 1e-12 * np.linalg.norm(u[isd])):
+                return u, k + 1
+        raise AssertionError("no convergence")
+
+    # same residual, different tangent, at a damaging trial state
+    (_, _), r_c = system(u0 * 1.0, False)
+    (_, _), r_s = system(u0 * 1.0, True)
+    np.testing.assert_array_equal(r_c, r_s)
+    u_n, it_n = solve(False)
+    u_s, it_s = solve(True)
+    D, _ = cm.damage(np.maximum(st.kappa_hist, el.gp_ebar(m, u_n).ravel()), mat.kappa0, mat.alpha, mat.beta)
+    assert D.max() > 0.0 and np.count_nonzero(D) > 0       # the step damages the notch tip
+    assert it_s > it_n                                     # linear against quadratic convergence
+    assert np.abs(u_s - u_n).max() <= 1e-9 * np.abs(u_n).max()
