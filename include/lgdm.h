@@ -161,7 +161,7 @@ lgdm_status lgdm_reset_state(lgdm_sim *sim);
 /* Copy a field (lgdm_field) into host memory of n doubles (n must match). */
 lgdm_status lgdm_get_field(lgdm_sim *sim, int32_t which, double *host_dst, size_t n);
 
-/* Start a load step (Algorithm 2, line 2): set the Dirichlet dofs of the
+/* Start a load step (Algorithm 2): set the Dirichlet dofs of the
  * committed state to dir_scale * load. */
 lgdm_status lgdm_begin_step(lgdm_sim *sim, double load);
 
@@ -177,12 +177,12 @@ lgdm_status lgdm_assemble(lgdm_sim *sim);
  * Dirichlet dofs).  Any pointer may be NULL to skip it. */
 lgdm_status lgdm_get_system(lgdm_sim *sim, int32_t *rowptr, int32_t *col, double *vals, double *rhs);
 
-/* Solve K delta = F (Algorithm 2, line 8) with BiCGSTAB preconditioned by the
+/* Solve K delta = F (Algorithm 2) with BiCGSTAB preconditioned by the
  * chosen Jacobi variant, one persistent launch; delta is kept on the device
  * (LGDM_FIELD_DELTA).  Synchronises; iters / rel_res may be NULL. */
 lgdm_status lgdm_solve(lgdm_sim *sim, int32_t *iters, double *rel_res);
 
-/* u += delta and the convergence test of Algorithm 2, line 18.  Synchronises. */
+/* u += delta and the convergence test of Algorithm 2.  Synchronises. */
 lgdm_status lgdm_update(lgdm_sim *sim, int32_t *converged);
 
 /* One Newton iteration: assemble, solve (BiCGSTAB; when it does not reach
@@ -248,9 +248,13 @@ lgdm_status lgdm_get_reaction(lgdm_sim *sim, double *reaction);
  * block size, walked by a tuned number of resident blocks); batched launches
  * gather the CSR values and set up the preconditioners; one cooperative
  * launch per wave solves the members' systems, each member on its own block
- * group and grid barrier with the group size it uses alone, so a member's
- * results are bitwise those of the member run alone.  The launches of a
- * Newton step up to the solve are captured once into a CUDA graph.  Members
+ * group (sized in proportion to its node count) with its own grid barrier.
+ * Inner products are summed over fixed node tiles, so a member's results do
+ * not depend on its group size: they are bitwise those of the member run
+ * alone.  A member whose consistent tangent defeats the Krylov solvers is
+ * assembled and solved again with the secant tangent in a second batched
+ * pass, exactly as lgdm_newton_step does alone.  The launches of a Newton
+ * step up to the solve are captured once into a CUDA graph.  Members
  * must have been created on the batch's stream with the same precision and
  * must not be driven individually while a batch call runs.  The batch
  * workspace (device, caller-owned, lgdm_batch_workspace_size bytes) holds
@@ -285,7 +289,7 @@ lgdm_status lgdm_batch_assemble(lgdm_batch *batch, const int32_t *active);
 lgdm_status lgdm_batch_enable_timers(lgdm_batch *batch, int32_t on);
 lgdm_status lgdm_batch_get_timers(lgdm_batch *batch, double *ms4, int64_t *count4, int32_t reset);
 
-/* One Newton iteration (Algorithm 2, lines 6-18) for the active members;
+/* One Newton iteration (Algorithm 2) for the active members;
  * converged[i] = 1 converged, 0 not yet, -1 non-finite (host arrays of n,
  * krylov_iters may be NULL).  Synchronises. */
 lgdm_status lgdm_batch_newton_step(lgdm_batch *batch, const int32_t *active, int32_t *converged,

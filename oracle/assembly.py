@@ -1,4 +1,4 @@
-"""Global assembly, Dirichlet handling and reaction (Algorithm 1 lines 9-11).
+"""Global assembly, Dirichlet handling and reaction (Algorithm 1).
 
 The element blocks are unrolled into (row, col, value) triplets and summed
 into a sparse matrix, as the paper's ``sparse(row, col, val)`` assembly does;

@@ -13,8 +13,8 @@
 // reports a timeout instead of hanging.
 //
 // mode 1 ends the launch with the Newton update u += delta and the
-// convergence test ||du|| <= tol ||u||, ||de|| <= tol ||e|| (Algorithm 2,
-// lines 9 and 18); mode 2 does only that update; mode 0 only solves.
+// convergence test ||du|| <= tol ||u||, ||de|| <= tol ||e|| (Algorithm 2);
+// mode 2 does only that update; mode 0 only solves.
 #include "lgdm_internal.cuh"
 #include <cuda/atomic>
 
