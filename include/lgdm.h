@@ -138,6 +138,13 @@ lgdm_status lgdm_default_options(lgdm_options *opt);
  * adjacency on the host to count the CSR pattern exactly. */
 lgdm_status lgdm_workspace_size(const lgdm_mesh *mesh, const lgdm_options *opt, size_t *bytes);
 
+/* Size of the fixed CSR pattern of this mesh, host only (no device call):
+ * npairs = node pairs (a, b) that share an element, a == b included; the
+ * node-block CSR holds nnz = nd * nd * npairs values (Sec. 2.2 assembles into
+ * this pattern).  Errors: LGDM_ERR_INVALID_ARG for a bad mesh (unknown
+ * element type, missing arrays, connectivity out of range). */
+lgdm_status lgdm_pattern_counts(const lgdm_mesh *mesh, int64_t *npairs, int64_t *nnz);
+
 /* Create a simulation.  Copies the mesh, material and conditions, builds the
  * node-block CSR pattern and the element-to-nonzero map on the host, uploads
  * them into dev_workspace (>= lgdm_workspace_size bytes, 256-byte aligned)

@@ -83,6 +83,7 @@ _SIGS = {
     "lgdm_last_solve": (C.c_int, [C.c_void_p, _ip, _ip, _dp, _dp]),
     "lgdm_get_reaction": (C.c_int, [C.c_void_p, _dp]),
     "lgdm_get_energy": (C.c_int, [C.c_void_p, _dp]),
+    "lgdm_pattern_counts": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
     "lgdm_enable_timers": (C.c_int, [C.c_void_p, C.c_int32]),
     "lgdm_get_timers": (C.c_int, [C.c_void_p, _dp, C.POINTER(C.c_int64)]),
     "lgdm_reset_timers": (C.c_int, [C.c_void_p]),

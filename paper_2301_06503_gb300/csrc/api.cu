@@ -476,6 +476,26 @@ lgdm_status lgdm_workspace_size(const lgdm_mesh *m, const lgdm_options *o, size_
   }
 }
 
+lgdm_status lgdm_pattern_counts(const lgdm_mesh *m, int64_t *npairs, int64_t *nnz) {
+  try {
+    if (!npairs || !nnz) return fail(nullptr, LGDM_ERR_INVALID_ARG, "NULL argument");
+    lgdm_status st = check_mesh(m);
+    if (st != LGDM_OK) return st;
+    Pattern P;
+    std::string err;
+    st = build_pattern(*m, P, false, err);
+    if (st != LGDM_OK) return fail(nullptr, st, err);
+    const int64_t nd = dim_of(m->elem) + 1;
+    *npairs = P.npairs;
+    *nnz = P.npairs * nd * nd;
+    return LGDM_OK;
+  } catch (const std::bad_alloc &) {
+    return fail(nullptr, LGDM_ERR_INVALID_ARG, "host out of memory while counting the pattern");
+  } catch (...) {
+    return fail(nullptr, LGDM_ERR_INVALID_ARG, "unexpected host exception");
+  }
+}
+
 lgdm_status lgdm_create(const lgdm_mesh *m, const lgdm_material *mat, const lgdm_bcs *bcs,
                         const lgdm_options *o, void *ws, size_t ws_bytes, void *stream, lgdm_sim **out) {
   lgdm_sim *s = nullptr;

@@ -59,6 +59,14 @@ class _MeshArgs:
                         _p(es, C.c_double), _p(vs, C.c_double))
 
 
+def pattern_counts(mesh):
+    """(node pairs, CSR nonzeros) of the mesh's fixed pattern; host only."""
+    m = _MeshArgs(mesh)
+    npairs, nnz = C.c_int64(), C.c_int64()
+    L.check(L.load().lgdm_pattern_counts(C.byref(m.s), C.byref(npairs), C.byref(nnz)))
+    return int(npairs.value), int(nnz.value)
+
+
 def workspace_bytes(mesh, **opts) -> int:
     m = _MeshArgs(mesh)
     n = C.c_size_t()
