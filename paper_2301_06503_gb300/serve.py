@@ -43,6 +43,8 @@ class Job:
     bytes: int = 0
     reactions: List[float] = field(default_factory=list)
     newton_iters: int = 0
+    krylov_iters: int = 0
+    psi: Optional[float] = None             # stored energy (Eq. 1) at the last committed state
     status: int = 0
 
     @property
@@ -52,6 +54,19 @@ class Job:
     @property
     def service_time(self):
         return None if self.finish is None else self.finish - self.admit
+
+    def record(self) -> dict:
+        """One line of the per-request log: times, iteration counts, peak load
+        and dissipated energy (external work by the trapezoid rule over the
+        served load steps minus the stored energy)."""
+        loads = [0.0] + [self.problem.load(n) for n in range(1, len(self.reactions) + 1)]
+        reac = [0.0] + list(self.reactions)
+        w_ext = sum(0.5 * (reac[k] + reac[k - 1]) * (loads[k] - loads[k - 1]) for k in range(1, len(reac)))
+        return {"rid": self.rid, "arrival": self.arrival, "admit": self.admit, "finish": self.finish,
+                "status": self.status, "load_steps": self.step, "newton_iters": self.newton_iters,
+                "krylov_iters": self.krylov_iters,
+                "peak_load": max(self.reactions) if self.reactions else None,
+                "dissipated_energy": (w_ext - self.psi) if self.psi is not None else None}
 
 
 class Server:
@@ -102,6 +117,9 @@ class Server:
         for job in self.resident:
             if job.step >= job.n_steps or job.status != 0:
                 job.finish = now
+                job.krylov_iters = job.sim.counters()["krylov_iters"]
+                if job.status == 0:
+                    job.psi = job.sim.energy()
                 job.sim.close()
                 job.sim = None
                 self.used -= job.bytes
@@ -180,6 +198,10 @@ class Server:
             "p99_service_s": float(np.percentile(svc, 99)) if ok else None,
             "ticks": self.ticks, "peak_resident_bytes": self.peak_used, "budget_bytes": self.budget,
         }
+
+    def records(self) -> List[dict]:
+        """Per-request log of the finished requests, in request order."""
+        return [j.record() for j in sorted(self.done, key=lambda j: j.rid)]
 
 
 def run_one_at_a_time(jobs: List[Job], precision: str = "fp64", stream=None, **sim_opts):

@@ -62,6 +62,12 @@ class _FakeSim:
     def reaction(self):
         return float(self.steps)
 
+    def counters(self):
+        return {"krylov_iters": 10 * self.steps}
+
+    def energy(self):
+        return 0.25
+
     def close(self):
         _FakeSim.live -= 1
 
@@ -128,6 +134,13 @@ def test_server_budget_slots_and_reuse(serve):
     # admission in arrival order: a job is admitted no earlier than the one before it
     admits = [j.admit for j in sorted(jobs, key=lambda j: j.rid)]
     assert all(a <= b for a, b in zip(admits, admits[1:]))
+    # per-request log: reactions 1, 2, 3 at loads 1, 2, 3 mm-thousandths
+    rec = srv.records()
+    assert [r["rid"] for r in rec] == list(range(len(jobs)))
+    r0 = rec[0]
+    assert r0["load_steps"] == 3 and r0["peak_load"] == 3.0 and r0["krylov_iters"] == 30
+    w_ext = 0.001 * (0.5 * (0 + 1) + 0.5 * (1 + 2) + 0.5 * (2 + 3))
+    assert abs(r0["dissipated_energy"] - (w_ext - 0.25)) <= 1e-15
 
 
 def test_server_retires_a_failed_request(serve):
