@@ -157,3 +157,68 @@ def test_server_refuses_a_request_larger_than_the_budget(serve):
     srv = serve.Server(budget_bytes=50, stream=object())
     with pytest.raises(ValueError):
         srv.submit(serve.Job(0, _Problem(51), 0.0, n_steps=1))
+
+
+# ------------------------------------------------------------------ bench line
+def _plate_stats(newton=30, kiters=34250):
+    import lgdm_inputs as li
+    m = li.sen_plate_problem().mesh
+    return m, {"gp": newton * m.nel * m.ngp, "newton": newton, "elem_integrations": newton * m.nel,
+               "krylov_iters": kiters, "halvings": 0, "launches": 175,
+               "phase_ms": {"element": 6.0, "gather": 1.64, "precond": 0.43, "krylov": 1898.6,
+                            "commit": 0.15, "begin_step": 0.05},
+               "phase_n": {"element": newton, "gather": newton, "precond": newton, "krylov": 2 * newton,
+                           "commit": 5, "begin_step": 5},
+               "elements": m.nel, "elem": m.elem, "nnode": m.nnode, "nel": m.nel, "nd": m.nd,
+               "nnz": 3250809, "npairs": 361201, "members": [(m.nnode, m.nd, 3250809, 361201, kiters)]}
+
+
+def test_bench_line_contract_and_rooflines():
+    """The JSON line built from a run's counters and phase times: contract
+    keys, throughput, and the roofline arithmetic of both kernels."""
+    import argparse
+    import bench
+    from paper_2301_06503_gb300 import roofline
+    m, st = _plate_stats()
+    args = argparse.Namespace(precision="fp64", steps=5, warmup=3, mode="loadstep")
+    pk = {"hbm_gbs": 6788.3, "hbm_src": "measured", "fp64_tflops": 1.25, "fp32_tflops": 75.0}
+    step_ms = [381.6] * 5
+    line = bench.summarize(args, "sen_plate_q4_200x200", 1, [m], st, step_ms, sum(step_ms) / 1e3, st["gp"], 1, pk,
+                           {"value": 1.0, "unit": "GP/s", "h2d_bytes_per_step": 1, "d2h_bytes_per_step": 1},
+                           None, {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": []})
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+              "scaling", "vs_baseline", "dtype", "data", "config", "roofline", "cpu_baseline", "e2e",
+              "gpu_launches", "clocks"):
+        assert k in line
+    assert line["value"] == st["gp"] / (sum(step_ms) / 1e3)
+    assert abs(line["ms_per_step"] - 381.6) < 1e-9
+    res_f, tan_f = roofline.element_flops(m.elem)
+    el = line["roofline_element"]
+    assert el["bound"] == "alu" and abs(el["achieved"] - m.nel * (res_f + tan_f) / 0.2e-3 / 1e12) < 1e-9
+    assert abs(el["frac"] - el["achieved"] / 1.25) < 1e-12
+    kr = line["roofline_krylov"]
+    fl, by = roofline.krylov_iteration(m.nnode, m.nd, 3250809, 361201, 8)
+    t_fl, t_by = fl / 1.25e12, by / 6788.3e9                # the slower of the two at its peak binds
+    if t_by > t_fl:
+        assert kr["bound"] == "hbm"
+        assert abs(kr["achieved"] - by * st["krylov_iters"] / (1898.6e-3) / 1e9) < 1e-6
+    else:
+        assert kr["bound"] == "alu"
+        assert abs(kr["achieved"] - fl * st["krylov_iters"] / (1898.6e-3) / 1e12) < 1e-9
+    assert abs(kr["frac"] - kr["achieved"] / kr["peak"]) < 1e-12
+    assert line["roofline"] is kr                           # the solve dominates this step
+    asm = line["assembly_only"]["value"]
+    assert abs(asm - st["gp"] / ((6.0 + 1.64 + 0.43) * 1e-3)) < 1e-3
+
+
+def test_bench_line_fp32_element_bound():
+    """FP32 tangent: the element roofline takes the slowest of the FP64
+    residual path, the FP32 tangent path and the bytes."""
+    import argparse
+    import bench
+    m, st = _plate_stats()
+    args = argparse.Namespace(precision="fp32", steps=2, warmup=3, mode="newton")
+    pk = {"hbm_gbs": 6788.3, "hbm_src": "measured", "fp64_tflops": 1.25, "fp32_tflops": 75.0}
+    line = bench.summarize(args, "x", 1, [m], st, [10.0, 10.0], 0.02, st["gp"], 1, pk, None, None, None)
+    el = line["roofline_element"]
+    assert el["bound"] == "alu" and el["peak"] == 1.25 and line["dtype"] == "f32-tangent/f64"
