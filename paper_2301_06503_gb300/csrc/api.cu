@@ -1132,8 +1132,10 @@ extern "C" lgdm_status lgdm_run_step(lgdm_sim *s, double load, int32_t *newton_i
 // Several simulations advanced together: one persistent element launch per
 // element type over all members' tiles, batched gather and preconditioner
 // set-up, one cooperative BiCGSTAB launch per wave of members (each member on
-// its own block group and barrier, with the group size it uses alone), the
-// batched update, and a CUDA graph of the launches of a Newton step.
+// its own block group and barrier; the tile sums make its result independent
+// of the group size), a second batched pass with the secant tangent for the
+// members whose solve failed, the batched update, and a CUDA graph of the
+// launches of a Newton step.
 struct lgdm_batch {
   std::vector<lgdm_sim *> sims;
   int n = 0;

@@ -448,8 +448,8 @@ __global__ void __launch_bounds__(KT) bicgstab_kernel(KrylovArgs A, int mode) {
 
 // Several independent systems in one cooperative launch: block b belongs to
 // the system s with group_start[s] <= b < group_start[s+1]; every system has
-// its own barrier words and partial sums, so its arithmetic and its result
-// are those of a launch of its group size alone.
+// its own barrier words and tile sums, so its arithmetic and its result are
+// those of the system solved alone, whatever its group size.
 template <int ND, typename TT>
 __global__ void __launch_bounds__(KT) bicgstab_grouped_kernel(const KrylovArgs *__restrict__ args,
                                                               const int32_t *__restrict__ members,
