@@ -137,6 +137,12 @@ class Sim:
         self._ck(self._lib.lgdm_reset_state(self.h))
 
     def field(self, which) -> np.ndarray:
+        """A field copied to the host: "u" (interleaved dofs), "displacement"
+        (nodes x dim), "ebar" (nodal micro-equivalent strain), "kappa_hist" and
+        "damage" (per Gauss point, element-major), "delta", "residual", "rhs"."""
+        if which in ("displacement", "ebar"):
+            u = self.field("u").reshape(-1, self.nd)
+            return u[:, :self.dim].copy() if which == "displacement" else u[:, self.dim].copy()
         which = {"u": L.FIELD_U, "kappa_hist": L.FIELD_KAPPA_HIST, "damage": L.FIELD_DAMAGE,
                  "delta": L.FIELD_DELTA, "residual": L.FIELD_RESIDUAL, "rhs": L.FIELD_RHS}.get(which, which)
         n = self.nel * self.ngp if which in (L.FIELD_KAPPA_HIST, L.FIELD_DAMAGE) else self.ndof
