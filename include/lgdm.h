@@ -142,7 +142,9 @@ lgdm_status lgdm_workspace_size(const lgdm_mesh *mesh, const lgdm_options *opt, 
  * npairs = node pairs (a, b) that share an element, a == b included; the
  * node-block CSR holds nnz = nd * nd * npairs values (Sec. 2.2 assembles into
  * this pattern).  Errors: LGDM_ERR_INVALID_ARG for a bad mesh (unknown
- * element type, missing arrays, connectivity out of range). */
+ * element type, missing arrays, connectivity out of range, a node that
+ * belongs to no element); lgdm_workspace_size and lgdm_create refuse the
+ * same meshes. */
 lgdm_status lgdm_pattern_counts(const lgdm_mesh *mesh, int64_t *npairs, int64_t *nnz);
 
 /* Create a simulation.  Copies the mesh, material and conditions, builds the

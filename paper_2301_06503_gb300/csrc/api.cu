@@ -39,6 +39,11 @@ lgdm_status build_pattern(const lgdm_mesh &m, Pattern &P, bool with_contrib, std
     }
     inc_ptr[n + 1]++;
   }
+  for (int32_t n = 0; n < nn; ++n)
+    if (inc_ptr[n + 1] == 0) {                 // its rows would be empty: a singular system
+      err = "node " + std::to_string(n) + " belongs to no element";
+      return LGDM_ERR_INVALID_ARG;
+    }
   for (int32_t n = 0; n < nn; ++n) inc_ptr[n + 1] += inc_ptr[n];
   std::vector<int32_t> inc(inc_ptr[nn]), fill(inc_ptr.begin(), inc_ptr.end() - 1);
   for (int32_t e = 0; e < ne; ++e)

@@ -86,3 +86,23 @@ def test_workspace_size_grows_with_the_mesh_and_shrinks_with_fp32():
     big = workspace_bytes(li.sen_plate_problem(40, 40).mesh)
     big32 = workspace_bytes(li.sen_plate_problem(40, 40).mesh, precision="fp32")
     assert 0 < small < big and big32 < big
+
+
+def test_empty_and_degenerate_meshes():
+    """An empty mesh, and one with a node that belongs to no element (its
+    rows would be empty), are refused before any device work; a single
+    element sizes correctly."""
+    import copy
+    from paper_2301_06503_gb300.sim import pattern_counts, workspace_bytes
+    m = copy.deepcopy(li.sen_plate_problem(3, 3).mesh)
+    m.conn = m.conn[:0]                              # no elements
+    with pytest.raises(_lib.LgdmError) as ei:
+        workspace_bytes(m)
+    assert ei.value.status == 1
+    one = li.sen_plate_problem(1, 1).mesh            # a single Q4
+    assert pattern_counts(one) == (16, 16 * 9)
+    spare = copy.deepcopy(li.sen_plate_problem(2, 2).mesh)
+    spare.conn = spare.conn[:1]                      # one element of a 3 x 3 node grid: 5 nodes unused
+    with pytest.raises(_lib.LgdmError) as ei:
+        pattern_counts(spare)
+    assert "belongs to no element" in str(ei.value)
