@@ -10,7 +10,9 @@ plate, first 30 load steps, ~30 CPU minutes), batch_plate8_step1 (plate 8
 of the 256-plate batch, 200 x 200, first load step: its Newton iterations
 pass through tangents that defeat the Jacobi-preconditioned Krylov solvers,
 ~1 CPU minute), and, only when named, sen_plate_60 (the 200 x 200 plate,
-60 load steps, 30 of them past the peak, a few CPU hours).
+60 load steps, 30 of them past the peak, a few CPU hours) and
+tpb_beam_40x8x8_90 (the notched beam at 40 x 8 x 8 hexahedra, first 90 of
+its 300 load steps, a few CPU hours).
 """
 import json
 import os
@@ -45,12 +47,13 @@ CASES = {
     "bar1d": lambda: ("bar_problem()", li.bar_problem(), 200),
     "sen_plate_prefix": lambda: ("sen_plate_problem()", li.sen_plate_problem(), 30),
     "sen_plate_60": lambda: ("sen_plate_problem()", li.sen_plate_problem(), 60),
+    "tpb_beam_40x8x8_90": lambda: ("tpb_beam_problem(40, 8, 8)", li.tpb_beam_problem(40, 8, 8), 90),
     "batch_plate8_step1": lambda: ("batch_plate_problems()[8]", li.batch_plate_problems()[8], 1),
 }
 
 
 def main(names):
-    for name in names or [n for n in CASES if n != "sen_plate_60"]:
+    for name in names or [n for n in CASES if n not in ("sen_plate_60", "tpb_beam_40x8x8_90")]:
         desc, p, n = CASES[name]()
         rec = {"problem": f"lgdm_inputs.{desc}", "steps": n,
                "source": "oracle/newton.run (numpy element integration, scipy SuperLU), tests/golden/make_golden.py"}
