@@ -93,7 +93,9 @@ def reaction_at(problem, state):
 
 
 def free_energy(problem, state, chunk=20000):
-    """Stored energy: integral of Eq. 1 at a committed state."""
+    """Stored energy: integral of Eq. 1 over the mesh at a state, with the
+    trial history max(kappa_hist, ebar) (at a committed state: kappa_hist).
+    A complex state (complex-step derivatives) gives a complex value."""
     mesh, mat = problem.mesh, problem.material
     total = 0.0
     for s in range(0, mesh.nel, chunk):
@@ -101,8 +103,17 @@ def free_energy(problem, state, chunk=20000):
         t = el.element_terms(mesh, mat, state.u, state.kappa_hist, elems)
         psi = cm.free_energy_density(t["D"], t["eps"], t["Ceps"], mat.h, t["eps_eq"],
                                      t["ebar"], t["g"], mat.c, t["gbar"])
-        total += float(np.sum(psi * t["dV"]))
-    return total
+        total = total + np.sum(psi * t["dV"])
+    return float(total) if np.isrealobj(total) else complex(total)
+
+
+def damaged_volume(problem, state, threshold):
+    """Volume of the region whose committed damage D(kappa_hist) (Eq. A.1)
+    exceeds ``threshold``: the sum of dV over those Gauss points."""
+    mesh, mat = problem.mesh, problem.material
+    _, dV = el.geometry(mesh, np.arange(mesh.nel))
+    D, _ = cm.damage(state.kappa_hist, mat.kappa0, mat.alpha, mat.beta)
+    return float(np.sum(dV.ravel()[D > threshold]))
 
 
 def run(problem, n_steps=None, state=None, first_step=1, energy=True):

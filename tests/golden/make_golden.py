@@ -10,7 +10,11 @@ plate, first 30 load steps, ~30 CPU minutes), batch_plate8_step1 (plate 8
 of the 256-plate batch, 200 x 200, first load step: its Newton iterations
 pass through tangents that defeat the Jacobi-preconditioned Krylov solvers,
 ~1 CPU minute), and, only when named, tpb_beam_40x8x8_90 (the notched beam
-at 40 x 8 x 8 hexahedra, first 90 of its 300 load steps, a few CPU hours).
+at 40 x 8 x 8 hexahedra, first 90 of its 300 load steps, a few CPU hours),
+trace_plate_r14_30 and trace_beam_r7_40 (requests 14 and 7 of the seeded
+serving trace: a 56 x 56 notched plate, first 30 load steps, and a 42 x 8 x 8
+notched beam, first 40 load steps; the served results are compared with
+them).
 The 200 x 200 plate has no displacement-controlled solution at step 32 (the
 oracle's Newton diverges there through all halvings), so its stored run
 ends at step 30.
@@ -49,11 +53,14 @@ CASES = {
     "sen_plate_prefix": lambda: ("sen_plate_problem()", li.sen_plate_problem(), 30),
     "tpb_beam_40x8x8_90": lambda: ("tpb_beam_problem(40, 8, 8)", li.tpb_beam_problem(40, 8, 8), 90),
     "batch_plate8_step1": lambda: ("batch_plate_problems()[8]", li.batch_plate_problems()[8], 1),
+    "trace_plate_r14_30": lambda: ("serving_trace()[14].problem", li.serving_trace()[14].problem, 30),
+    "trace_beam_r7_40": lambda: ("serving_trace()[7].problem", li.serving_trace()[7].problem, 40),
 }
+ONLY_WHEN_NAMED = ("tpb_beam_40x8x8_90", "trace_plate_r14_30", "trace_beam_r7_40")
 
 
 def main(names):
-    for name in names or [n for n in CASES if n != "tpb_beam_40x8x8_90"]:
+    for name in names or [n for n in CASES if n not in ONLY_WHEN_NAMED]:
         desc, p, n = CASES[name]()
         rec = {"problem": f"lgdm_inputs.{desc}", "steps": n,
                "source": "oracle/newton.run (numpy element integration, scipy SuperLU), tests/golden/make_golden.py"}

@@ -16,8 +16,20 @@ Each test names the pin it implements:
   P8  history and damage irreversible and bounded over committed steps
   P10 sparse assembly = brute-force dense sum of element blocks; dof map
   P11 dissipated energy non-negative and non-decreasing
+  P11b stored energy (Eq. 1) in closed form: in homogeneous elastic states
+      (uniform bar, 2D plane-strain and 3D uniaxial stress) it equals
+      1/2 sigma:eps V and the external work of the reaction
+  P11c stored energy derivatives: with the history frozen (no loading point)
+      d Psi / d ebar is the micro-strain residual (Eq. 11f) and, with h = 0,
+      d Psi / d u is the displacement residual (Eq. 11e)
+  P12 increment halving: a forced halving commits the midpoint and equals
+      the two sub-steps taken explicitly, each from its committed state
   P13 tangent structure: K_uu symmetric, K_ue = 0 without loading points
+  P14 damaged-region volume: sum of dV over the Gauss points with D above a
+      threshold equals the volume of the elements built to carry that damage
 """
+import dataclasses
+
 import numpy as np
 import pytest
 
@@ -427,3 +439,141 @@ def test_secant_tangent_same_residual_and_root():
     assert D.max() > 0.0 and np.count_nonzero(D) > 0       # the step damages the notch tip
     assert it_s > it_n                                     # linear against quadratic convergence
     assert np.abs(u_s - u_n).max() <= 1e-9 * np.abs(u_n).max()
+
+
+# ---------------------------------------------------------------- P11b, P11c
+def _trapezoid_work(loads, reactions):
+    lp = np.concatenate([[0.0], loads])
+    rp = np.concatenate([[0.0], reactions])
+    return np.cumsum(0.5 * (rp[1:] + rp[:-1]) * np.diff(lp))
+
+
+def test_p11b_stored_energy_closed_forms():
+    """Homogeneous elastic states: the micro-strain equals the (uniform) local
+    equivalent strain, so the h-terms of Eq. 1 vanish and Psi = 1/2 sigma eps V
+    exactly; the response is linear, so the trapezoid external work of the
+    reaction is exact and equals Psi too."""
+    # uniform bar: Psi = 1/2 E A L eps^2
+    p = li.bar_problem(weak_factor=1.0, n_steps=200)
+    out = nw.run(p, n_steps=3)
+    eps = out["load"] / 100.0
+    closed = 0.5 * p.material.E * 10.0 * 100.0 * eps ** 2
+    np.testing.assert_allclose(out["psi"], closed, rtol=1e-12)
+    np.testing.assert_allclose(_trapezoid_work(out["load"], out["reaction"]), closed, rtol=1e-12)
+    # plane strain, uniaxial stress (distorted interior): Psi = 1/2 E/(1-nu^2) eps_yy^2 V
+    m = li.plate_q4(4, 3, 4.0, 3.0)
+    inner = (m.x > 0) & (m.x < 4.0) & (m.y > 0) & (m.y < 3.0)
+    m.x[inner] += 0.15 * np.sin(3 * m.y[inner])
+    bottom, top = np.arange(5), 15 + np.arange(5)
+    left = np.arange(4) * 5
+    bcs = li.BCs(np.concatenate([li.node_dofs(m, bottom, 1), li.node_dofs(m, left, 0),
+                                 li.node_dofs(m, top, 1)]),
+                 np.concatenate([np.zeros(5), np.zeros(4), np.ones(5)]))
+    mat = _no_damage(MAT)
+    p2 = li.Problem("uniax2d", m, mat, bcs, u_max=3e-4, n_steps=3)
+    out = nw.run(p2)
+    eyy = out["load"] / 3.0
+    closed = 0.5 * mat.E / (1 - mat.nu ** 2) * eyy ** 2 * 12.0
+    np.testing.assert_allclose(out["psi"], closed, rtol=1e-12)
+    np.testing.assert_allclose(_trapezoid_work(out["load"], out["reaction"]), closed, rtol=1e-12)
+    # 3D uniaxial stress: Psi = 1/2 E eps_zz^2 V
+    m3 = li.beam_h8(3, 2, 2, 3.0, 2.0, 2.0)
+    X = m3.coords()
+    f = lambda mask: np.nonzero(mask)[0]
+    groups = [(f(X[:, 0] == 0), 0, 0.0), (f(X[:, 1] == 0), 1, 0.0), (f(X[:, 2] == 0), 2, 0.0),
+              (f(X[:, 2] == 2.0), 2, 1.0)]
+    bcs3 = li.BCs(np.concatenate([li.node_dofs(m3, n, c) for n, c, _ in groups]),
+                  np.concatenate([np.full(len(n), v) for n, _, v in groups]))
+    p3 = li.Problem("uniax3d", m3, mat, bcs3, u_max=4e-4, n_steps=3)
+    out = nw.run(p3)
+    ezz = out["load"] / 2.0
+    closed = 0.5 * mat.E * ezz ** 2 * 12.0
+    np.testing.assert_allclose(out["psi"], closed, rtol=1e-12)
+    np.testing.assert_allclose(_trapezoid_work(out["load"], out["reaction"]), closed, rtol=1e-12)
+
+
+@pytest.mark.parametrize("mi", [0, 1, 2])
+def test_p11c_stored_energy_gradient_is_residual(mi):
+    """With kappa_hist above every micro-strain (chi = 0) D and g are fixed, so
+    Eq. 1 is a function of u and ebar whose partial derivatives are the
+    residuals: d Psi / d ebar_a = r_e[a] (the N h (ebar - eps_eq) and
+    g h c grad(ebar) terms, Eq. 11f) and, with h = 0, d Psi / d u = r_u
+    (the (1 - D) C eps term, Eq. 11e).  Complex-step derivatives."""
+    mesh = list(_small_meshes())[mi]
+    base = MAT if mesh.dim > 1 else li.Material(nu=0.0, k=1.0)
+    u, kh = li.random_state(mesh, seed=40 + mi, kappa0=base.kappa0)
+    ebar = el.gp_ebar(mesh, u).ravel()
+    kh = np.maximum(kh, ebar + 0.1 * base.kappa0)               # no loading point
+    assert np.any(kh > base.kappa0)                             # damaged points present
+    is_e = (np.arange(mesh.ndof) % mesh.nd) == mesh.dim
+    for mat, dofs, part in ((base, np.nonzero(is_e)[0], "e"),
+                            (dataclasses.replace(base, h=0.0), np.nonzero(~is_e)[0], "u")):
+        prob = li.Problem("p11c", mesh, mat, li.BCs(np.zeros(0, np.int32), np.zeros(0)), 1.0, 1)
+        _, r = asm.assemble(mesh, mat, u, kh, with_tangent=False)
+        hstep = 1e-30
+        grad = np.empty(len(dofs))
+        for k, j in enumerate(dofs):
+            uc = u.astype(complex)
+            uc[j] += 1j * hstep
+            grad[k] = nw.free_energy(prob, nw.State(uc, kh)).imag / hstep
+        ref = r[dofs]
+        assert np.abs(ref).max() > 0.0
+        assert np.abs(grad - ref).max() <= 1e-10 * np.abs(ref).max(), part
+
+
+# ---------------------------------------------------------------- P12
+def test_p12_forced_halving_equals_explicit_substeps():
+    """Plate 10 x 10, 30 load steps: step 5 needs 24 Newton iterations from the
+    committed state of step 4.  With max_newton = 16 the full increment fails
+    and is halved once; the result must be the midpoint step committed and
+    then the target step, each started from the committed state before it."""
+    p = li.sen_plate_problem(10, 10, n_steps=30)
+    st = nw.initial_state(p)
+    for n in range(1, 5):
+        st, _ = nw.advance(p, st, p.load(n))
+    q = dataclasses.replace(p, max_newton=16)
+    halved, its = nw.advance(q, st, q.load(5))
+    assert len(its) == 3 and its[0] == 16 and max(its[1:]) < 16     # one failure, two sub-steps
+    mid = 0.5 * (p.load(4) + p.load(5))
+    u1, _ = nw.newton(q, st, mid)
+    s1 = nw.commit(q, st, u1, mid)
+    u2, _ = nw.newton(q, s1, q.load(5))
+    s2 = nw.commit(q, s1, u2, q.load(5))
+    assert halved.load == q.load(5)
+    np.testing.assert_allclose(halved.u, s2.u, rtol=0, atol=1e-12 * np.abs(s2.u).max())
+    np.testing.assert_allclose(halved.kappa_hist, s2.kappa_hist, rtol=1e-12)
+    assert np.any(s1.kappa_hist > st.kappa_hist)                   # the midpoint commit moved the history
+    # the unhalved step needs 24 iterations; its state differs from the halved
+    # one because the committed midpoint raised the history (Eq. A.2) at
+    # points that unload afterwards: the response is path dependent
+    _, its_full = nw.advance(p, st, p.load(5))
+    assert its_full == [24]
+
+
+# ---------------------------------------------------------------- P14
+def test_p14_damaged_volume():
+    """Plate 6 x 4 on 60 x 40 mm with skewed interior nodes: the history of
+    the Gauss points of a chosen set of elements is put where D > 0.9 and
+    every other point below; the damaged volume is the area of that set
+    (the shoelace area of each element), and 0 or the whole area at the
+    extreme thresholds."""
+    m = li.plate_q4(6, 4, 60.0, 40.0)
+    inner = (m.x > 0) & (m.x < 60.0) & (m.y > 0) & (m.y < 40.0)
+    m.x[inner] += 2.0 * np.sin(m.y[inner])
+    mat = MAT
+    p = li.Problem("p14", m, mat, li.BCs(np.zeros(0, np.int32), np.zeros(0)), 1.0, 1)
+    chosen = np.array([2, 3, 9, 14, 15, 20])
+    kh = np.full((m.nel, m.ngp), 1.5 * mat.kappa0)                # D small
+    kh[chosen] = 200.0 * mat.kappa0                                # D > 0.9
+    D, _ = cm.damage(kh, mat.kappa0, mat.alpha, mat.beta)
+    assert D[chosen].min() > 0.9 and np.delete(D, chosen, axis=0).max() < 0.9
+    st = nw.State(np.zeros(m.ndof), kh.ravel())
+    X = m.coords()
+
+    def area(e):
+        xy = X[m.conn[e]]
+        return 0.5 * abs(np.dot(xy[:, 0], np.roll(xy[:, 1], -1)) - np.dot(xy[:, 1], np.roll(xy[:, 0], -1)))
+
+    np.testing.assert_allclose(nw.damaged_volume(p, st, 0.9), sum(area(e) for e in chosen), rtol=1e-13)
+    np.testing.assert_allclose(nw.damaged_volume(p, st, 0.0), 2400.0, rtol=1e-13)
+    assert nw.damaged_volume(p, st, 0.999999) == 0.0
