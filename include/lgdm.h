@@ -39,7 +39,7 @@
 extern "C" {
 #endif
 
-#define LGDM_ABI_VERSION 1
+#define LGDM_ABI_VERSION 2
 
 typedef enum {
   LGDM_OK = 0,
@@ -114,6 +114,10 @@ typedef struct {
   int32_t krylov_blocks;      /* 0 = as many co-resident blocks as fit            */
   int32_t gmres_m;            /* restart of GMRES (1..128); 0 = no GMRES          */
   int32_t krylov_method;      /* 0 BiCGSTAB, GMRES when it falls short; 1 GMRES    */
+  double wait_limit_s;        /* limit of every device-side wait (the Krylov grid
+                                 barrier): a wait that runs longer gives up, the
+                                 launch returns and the call reports
+                                 LGDM_ERR_TIMEOUT; 1e-6 .. 60 s, default 2 s      */
 } lgdm_options;
 
 typedef struct lgdm_sim lgdm_sim;
@@ -131,7 +135,7 @@ const char *lgdm_status_string(lgdm_status s);
 
 /* Fill *opt with the defaults (FP64, node-block Jacobi, tol 1e-8, rtol 1e-8,
  * 50 Newton iterations, 5000 Krylov iterations, 6 halvings, GMRES(64)
- * fallback). */
+ * fallback, 2 s device wait limit). */
 lgdm_status lgdm_default_options(lgdm_options *opt);
 
 /* Device workspace bytes the simulation of this mesh needs.  Builds the node
@@ -160,8 +164,25 @@ const char *lgdm_last_error(const lgdm_sim *sim);
 lgdm_status lgdm_get_sizes(const lgdm_sim *sim, lgdm_sizes *out);
 
 /* Replace the state from host arrays u [ndof] and kappa_hist [nelem*ngp]
- * (either may be NULL to keep it).  The result is also the committed state. */
+ * (either may be NULL to keep it).  The result is also the committed state.
+ * Both arrays are checked on the host first: a NaN or an infinity returns
+ * LGDM_ERR_NONFINITE and leaves the state unchanged.  The committed load,
+ * external work and reaction are kept (see lgdm_set_committed). */
 lgdm_status lgdm_set_state(lgdm_sim *sim, const double *u, const double *kappa_hist);
+
+/* Scalars of the committed state: the load parameter of the last committed
+ * load step, the external work W_ext accumulated by the trapezoid rule over
+ * the committed load-reaction points (R17: W_ext(n) = W_ext(n-1) + (R(n) +
+ * R(n-1)) (load(n) - load(n-1)) / 2, starting from 0 at the initial state),
+ * and the reaction at the committed state.  The points of that curve are
+ * the end points of the load steps (one per lgdm_run_step, or per
+ * lgdm_commit called by the caller); the committed midpoints of halved
+ * increments inside lgdm_run_step are not points of it.  Together with the U and
+ * KAPPA_HIST fields they are a checkpoint: lgdm_set_state followed by
+ * lgdm_set_committed resumes a simulation exactly.  get synchronises; any
+ * pointer may be NULL. */
+lgdm_status lgdm_get_committed(lgdm_sim *sim, double *load, double *external_work, double *reaction);
+lgdm_status lgdm_set_committed(lgdm_sim *sim, double load, double external_work, double reaction);
 
 /* Return to the initial state on the device (u = 0, kappa_hist = kappa0,
  * committed load 0) without re-creating the simulation.  Asynchronous. */
@@ -251,6 +272,32 @@ lgdm_status lgdm_get_energy(lgdm_sim *sim, double *psi);
 /* Reaction at the last committed state.  Synchronises. */
 lgdm_status lgdm_get_reaction(lgdm_sim *sim, double *reaction);
 
+/* Dissipated energy at the committed state (R17): the external work of
+ * lgdm_get_committed minus the stored energy Psi of Eq. 1 (lgdm_get_energy).
+ * Uses the assembly scratch: call it between load steps.  Synchronises;
+ * psi (may be NULL) receives the stored energy. */
+lgdm_status lgdm_get_dissipated_energy(lgdm_sim *sim, double *dissipated, double *psi);
+
+/* Volume of the region whose committed damage D(kappa_hist) (Eq. A.1)
+ * exceeds `threshold` (e.g. 0.9, the localised zone of Sec. 3.3): the sum of
+ * the integration weights dV = w det(J) vol_scale over those Gauss points,
+ * in fixed order.  Synchronises. */
+lgdm_status lgdm_get_damaged_volume(lgdm_sim *sim, double threshold, double *volume);
+
+/* Failure injection for tests of the failure paths; nothing here faults the
+ * GPU.  kind:
+ *   1  the next Krylov launch of this simulation waits at its grid barrier
+ *      for one block more than it launched: no block passes, every wait
+ *      gives up after wait_limit_s, the launch returns and the call reports
+ *      LGDM_ERR_TIMEOUT (the device context stays usable);
+ *   2  the next assembly sees a NaN in the current dofs (written into the
+ *      device state by the library): the solve reports a non-finite right-
+ *      hand side, lgdm_newton_step returns LGDM_ERR_NONFINITE, and
+ *      lgdm_run_step treats it like a diverged Newton iteration (the
+ *      increment is halved from the clean committed state);
+ *   0  clears a pending injection. */
+lgdm_status lgdm_inject_fault(lgdm_sim *sim, int32_t kind);
+
 /* ---------------------------------------------------------------- batches
  * Several simulations advanced together on one stream.  Per element type,
  * one persistent launch integrates every member's elements (tiles of a tuned
@@ -315,10 +362,9 @@ lgdm_status lgdm_batch_run_step(lgdm_batch *batch, const double *loads, int32_t 
  * For callers that cannot allocate device memory (a host framework that has
  * reserved all of it, a plugin that must not touch the CUDA allocator): the
  * working storage -- Krylov vectors, block inverses, partial sums, barrier
- * words -- comes from one statically reserved 64 MiB device array held by
- * every GPU that loads this library until the process exits.  The paper has
- * no counterpart; this is the same solver as lgdm_solve on a caller-held
- * system.
+ * words, result -- comes from one statically declared 64 MiB device array.
+ * The paper has no counterpart; this is the same solver as lgdm_solve on a
+ * caller-held system.
  *
  *   nd, nnode  dofs per node (2..4) and nodes; ndof = nd * nnode
  *   nbr_ptr    device int32 [nnode+1]; nbr device int32 [nbr_ptr[nnode]]:
@@ -330,14 +376,26 @@ lgdm_status lgdm_batch_run_step(lgdm_batch *batch, const double *loads, int32_t 
  *   rhs, x     device double [ndof]; x receives the solution (x = 0 start)
  *   rtol       stop when ||b - K x|| <= rtol ||b||; max_iter iteration cap
  *   stream     cudaStream_t (NULL = default stream); the call synchronises it
- *   iters, rel_res  may be NULL
+ *   iters, rel_res  may be NULL; written only when the solve ran to an end
+ *              (not on LGDM_ERR_TIMEOUT)
  *
- * The first call on a device looks up the array's device address once, with
- * that device current; make that first call before any stream capture.
- * Systems whose scratch exceeds the array (about 80 bytes per dof) are
- * rejected with LGDM_ERR_OOM and a message (lgdm_last_error(NULL)).  All
- * calls share the array and it keeps the previous call's contents (the
- * barrier words and the result are cleared at each call): calls that overlap
+ * When the array is reserved: CUDA loads a library's device code lazily, so
+ * the 64 MiB are reserved on a device the first time this entry point runs
+ * there (it then also looks up the array's device address, once per device,
+ * with that device current; make that first call before any stream
+ * capture).  A call with nnode == 0 does only this set-up and returns
+ * LGDM_OK: a caller that is about to reserve all remaining device memory
+ * makes it first.  If the reservation itself fails the call returns
+ * LGDM_ERR_OOM.  The array then stays reserved until the process exits.
+ *
+ * Size limit: the scratch takes 72 + 8 nd + 4 / nd bytes per dof (9 vectors,
+ * the nd x nd block inverses, one diagonal index per node) plus 96 bytes per
+ * reduction tile, each piece rounded up to 256 bytes: at most about 745 k
+ * dofs for nd = 2, 689 k for nd = 3 and 639 k for nd = 4.  Larger systems are
+ * rejected with LGDM_ERR_OOM and a message (lgdm_last_error(NULL)) before
+ * anything is launched.  All calls share the array and it keeps the previous
+ * call's contents (the barrier words and the result block are cleared at
+ * each call, every vector is written before it is read): calls that overlap
  * on the GPU, from any thread or stream, race and must be serialised. */
 lgdm_status lgdm_solve_noalloc(int32_t nd, int32_t nnode, const int32_t *nbr_ptr, const int32_t *nbr,
                                const double *vals, const double *rhs, double *x, double rtol,

@@ -21,6 +21,9 @@ STATUS = {0: "ok", 1: "invalid argument", 2: "workspace too small", 3: "CUDA err
           4: "Newton did not converge", 5: "non-finite value", 6: "device wait timed out",
           7: "call out of order"}
 
+ABI_VERSION = 2
+FAULT_NONE, FAULT_BARRIER_TIMEOUT, FAULT_NAN_STATE = 0, 1, 2
+
 _dp = C.POINTER(C.c_double)
 _ip = C.POINTER(C.c_int32)
 
@@ -44,7 +47,7 @@ class Options(C.Structure):
     _fields_ = [("precision", C.c_int32), ("precond", C.c_int32), ("newton_tol", C.c_double),
                 ("krylov_rtol", C.c_double), ("max_newton", C.c_int32), ("max_krylov", C.c_int32),
                 ("max_halvings", C.c_int32), ("krylov_blocks", C.c_int32), ("gmres_m", C.c_int32),
-                ("krylov_method", C.c_int32)]
+                ("krylov_method", C.c_int32), ("wait_limit_s", C.c_double)]
 
 
 class Sizes(C.Structure):
@@ -83,6 +86,11 @@ _SIGS = {
     "lgdm_last_solve": (C.c_int, [C.c_void_p, _ip, _ip, _dp, _dp]),
     "lgdm_get_reaction": (C.c_int, [C.c_void_p, _dp]),
     "lgdm_get_energy": (C.c_int, [C.c_void_p, _dp]),
+    "lgdm_get_committed": (C.c_int, [C.c_void_p, _dp, _dp, _dp]),
+    "lgdm_set_committed": (C.c_int, [C.c_void_p, C.c_double, C.c_double, C.c_double]),
+    "lgdm_get_dissipated_energy": (C.c_int, [C.c_void_p, _dp, _dp]),
+    "lgdm_get_damaged_volume": (C.c_int, [C.c_void_p, C.c_double, _dp]),
+    "lgdm_inject_fault": (C.c_int, [C.c_void_p, C.c_int32]),
     "lgdm_pattern_counts": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
     "lgdm_enable_timers": (C.c_int, [C.c_void_p, C.c_int32]),
     "lgdm_get_timers": (C.c_int, [C.c_void_p, _dp, C.POINTER(C.c_int64)]),
@@ -121,7 +129,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         fn = getattr(lib, name)
         fn.restype = res
         fn.argtypes = args
-    if lib.lgdm_abi_version() != 1:
+    if lib.lgdm_abi_version() != ABI_VERSION:
         raise RuntimeError("LGDM ABI version mismatch")
     _lib = lib
     return lib

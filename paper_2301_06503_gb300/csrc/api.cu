@@ -4,6 +4,7 @@
 #include "lgdm_internal.cuh"
 
 #include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -159,7 +160,11 @@ struct lgdm_sim {
   double *gm_V = nullptr, *gm_R = nullptr, *gm_y = nullptr, *gm_dots = nullptr, *gm_final = nullptr;
   int64_t gm_ld = 0;
   int gmres_blocks = 1;
-  double *partial = nullptr, *field_tmp = nullptr, *reaction = nullptr;
+  double *partial = nullptr, *field_tmp = nullptr;
+  // committed-state scalars on the device: [0] reaction, [1] external work
+  // (trapezoid rule over the committed load-reaction points), [2] reaction
+  // of the commit before
+  double *reaction = nullptr;
   unsigned int *bar = nullptr;
   SolveResult *res = nullptr;
   int krylov_blocks = 1;
@@ -187,8 +192,14 @@ struct lgdm_sim {
   // host copies
   std::vector<int32_t> h_nbr_ptr, h_nbr;
   std::string err;
-  double load_commit = 0.0;
+  double load_commit = 0.0, load_trial = 0.0;
+  // external work: the load of the last point of the load-reaction curve it
+  // covers, and whether commits are internal sub-steps of a halved load step
+  // (not points of the curve)
+  double load_point = 0.0;
+  bool substep_commits = false;
   bool assembled = false;
+  int fault = 0;                       // pending failure injection (lgdm_inject_fault)
 
   ~lgdm_sim() {
     for (auto &p : ev_pending) {
@@ -325,7 +336,7 @@ void carve(lgdm_sim &s, Carver &c) {
   }
   s.partial = c.take<double>((size_t)3 * 4 * krylov_ntiles(s.nnode));
   s.field_tmp = c.take<double>(std::max((size_t)s.nel * s.ngp, (size_t)s.ndof) + 64);   // + energy block sums
-  s.reaction = c.take<double>(1);
+  s.reaction = c.take<double>(3);
   s.bar = c.take<unsigned int>(2);
   s.res = c.take<SolveResult>(1);
   s.d_self = c.take<BatchSim>(1);
@@ -452,6 +463,7 @@ lgdm_status lgdm_default_options(lgdm_options *o) {
   o->krylov_blocks = 0;
   o->gmres_m = 64;
   o->krylov_method = 0;
+  o->wait_limit_s = 2.0;
   return LGDM_OK;
 }
 
@@ -519,6 +531,8 @@ lgdm_status lgdm_create(const lgdm_mesh *m, const lgdm_material *mat, const lgdm
       return fail(nullptr, LGDM_ERR_INVALID_ARG, "gmres_m must be in 0..128");
     if (o->krylov_method != 0 && !(o->krylov_method == 1 && o->gmres_m > 0))
       return fail(nullptr, LGDM_ERR_INVALID_ARG, "krylov_method 1 (GMRES) needs gmres_m > 0");
+    if (!(o->wait_limit_s >= 1e-6 && o->wait_limit_s <= 60.0))
+      return fail(nullptr, LGDM_ERR_INVALID_ARG, "wait_limit_s must be in 1e-6 .. 60 s");
     if (bcs && bcs->n_dir > 0 && (!bcs->dir_dof || !bcs->dir_scale))
       return fail(nullptr, LGDM_ERR_INVALID_ARG, "Dirichlet arrays missing");
     s = new lgdm_sim();
@@ -598,7 +612,7 @@ lgdm_status lgdm_create(const lgdm_mesh *m, const lgdm_material *mat, const lgdm
     e = e ? e : up(s->kappa_hist, kh.data(), sizeof(double) * kh.size());
     e = e ? e : cudaMemsetAsync(s->u, 0, sizeof(double) * s->ndof, st_);
     e = e ? e : cudaMemsetAsync(s->u_commit, 0, sizeof(double) * s->ndof, st_);
-    e = e ? e : cudaMemsetAsync(s->reaction, 0, sizeof(double), st_);
+    e = e ? e : cudaMemsetAsync(s->reaction, 0, 3 * sizeof(double), st_);
     e = e ? e : cudaMemsetAsync(s->res, 0, sizeof(SolveResult), st_);
     BatchSim self{};
     KrylovArgs kself{};
@@ -661,6 +675,13 @@ lgdm_status lgdm_get_sizes(const lgdm_sim *s, lgdm_sizes *o) {
 
 lgdm_status lgdm_set_state(lgdm_sim *s, const double *u, const double *kh) {
   if (!s) return fail(nullptr, LGDM_ERR_INVALID_ARG, "NULL handle");
+  if (u)
+    for (int64_t k = 0; k < s->ndof; ++k)
+      if (!std::isfinite(u[k])) return fail(s, LGDM_ERR_NONFINITE, "u[" + std::to_string(k) + "] is not finite");
+  if (kh)
+    for (int64_t k = 0; k < (int64_t)s->nel * s->ngp; ++k)
+      if (!std::isfinite(kh[k]))
+        return fail(s, LGDM_ERR_NONFINITE, "kappa_hist[" + std::to_string(k) + "] is not finite");
   if (u) {
     LGDM_CUDA(s, cudaMemcpyAsync(s->u, u, sizeof(double) * s->ndof, cudaMemcpyHostToDevice, s->stream));
     LGDM_CUDA(s, cudaMemcpyAsync(s->u_commit, s->u, sizeof(double) * s->ndof, cudaMemcpyDeviceToDevice, s->stream));
@@ -681,9 +702,9 @@ lgdm_status lgdm_reset_state(lgdm_sim *s) {
   LGDM_CUDA(s, cudaMemsetAsync(s->u, 0, sizeof(double) * s->ndof, s->stream));
   LGDM_CUDA(s, cudaMemsetAsync(s->u_commit, 0, sizeof(double) * s->ndof, s->stream));
   LGDM_CUDA(s, launch_fill(s->kappa_hist, (int64_t)s->nel * s->ngp, s->mat.kappa0, s->stream));
-  LGDM_CUDA(s, cudaMemsetAsync(s->reaction, 0, sizeof(double), s->stream));
+  LGDM_CUDA(s, cudaMemsetAsync(s->reaction, 0, 3 * sizeof(double), s->stream));
   s->counters[0] += 1;
-  s->load_commit = 0.0;
+  s->load_commit = s->load_trial = s->load_point = 0.0;
   s->assembled = false;
   s->secant = 0;
   s->secant_streak = 0;
@@ -722,6 +743,7 @@ lgdm_status lgdm_begin_step(lgdm_sim *s, double load) {
   // steps needed the secant one (then every 8th step tries it again)
   s->secant = (s->secant_streak > 0 && s->secant_streak % 8 != 0) ? 1 : 0;
   s->step_secant = false;
+  s->load_trial = load;
   LGDM_CUDA(s, cudaMemcpyAsync(s->u, s->u_commit, sizeof(double) * s->ndof, cudaMemcpyDeviceToDevice, s->stream));
   LGDM_CUDA(s, launch_set_dirichlet(s->u, s->dir_dof, s->dir_scale, s->ndir, load, s->stream));
   s->counters[0] += 1;
@@ -731,6 +753,12 @@ lgdm_status lgdm_begin_step(lgdm_sim *s, double load) {
 
 lgdm_status lgdm_assemble(lgdm_sim *s) {
   if (!s) return fail(nullptr, LGDM_ERR_INVALID_ARG, "NULL handle");
+  if (s->fault == 2) {                         // injected: a NaN in the current dofs
+    static const double nan_value = std::nan("");
+    s->fault = 0;
+    LGDM_CUDA(s, cudaMemcpyAsync(s->u + (int64_t)s->nd * (s->nnode / 2), &nan_value, sizeof(double),
+                                 cudaMemcpyHostToDevice, s->stream));
+  }
   if (s->secant != s->secant_dev) {            // the tangent mode lives in the device descriptor
     s->secant_dev = s->secant;
     char *dst = reinterpret_cast<char *>(s->d_self) + offsetof(BatchSim, mc) + offsetof(MatConst, secant);
@@ -843,6 +871,8 @@ KrylovArgs krylov_args(lgdm_sim *s) {
   a.bar_count = s->bar;
   a.bar_gen = s->bar + 1;
   a.res = s->res;
+  a.wait_ns = (unsigned long long)(s->opt.wait_limit_s * 1e9);
+  a.barrier_extra = 0;
   return a;
 }
 
@@ -850,22 +880,35 @@ lgdm_status finish_launch(lgdm_sim *s, int mode, SolveResult *out) {
   s->counters[0] += 1;
   LGDM_CUDA(s, cudaMemcpyAsync(out, s->res, sizeof(SolveResult), cudaMemcpyDeviceToHost, s->stream));
   LGDM_CUDA(s, cudaStreamSynchronize(s->stream));
-  if (mode != 2) s->counters[2] += out->iters;
   if (s->timers_on) resolve_timers(s);
+  if (out->status == 4) {
+    s->last.status = 4;
+    return fail(s, LGDM_ERR_TIMEOUT, "grid barrier timed out in the Krylov launch");
+  }
+  if (mode != 2) s->counters[2] += out->iters;
   if (mode == 2) {
     s->last.converged = out->converged;
     for (int k = 0; k < 4; ++k) s->last.norms[k] = out->norms[k];
   } else {
     s->last = *out;
   }
-  if (out->status == 4) return fail(s, LGDM_ERR_TIMEOUT, "grid barrier timed out in the Krylov launch");
   if (out->status == 3) return fail(s, LGDM_ERR_NONFINITE, "non-finite value in the Krylov solve or update");
   return LGDM_OK;
 }
 
+// Writes the barrier_extra word of the simulation's Krylov descriptor.
+cudaError_t set_barrier_extra(lgdm_sim *s, int v) {
+  static const int32_t values[2] = {0, 1};
+  char *dst = reinterpret_cast<char *>(s->d_kself) + offsetof(KrylovArgs, barrier_extra);
+  return cudaMemcpyAsync(dst, &values[v ? 1 : 0], sizeof(int32_t), cudaMemcpyHostToDevice, s->stream);
+}
+
 lgdm_status run_krylov(lgdm_sim *s, int mode, SolveResult *out) {
-  const KrylovArgs a = krylov_args(s);
-  (void)a;
+  const bool inject = s->fault == 1;
+  if (inject) {                                // injected: the barrier waits for a block that never comes
+    s->fault = 0;
+    LGDM_CUDA(s, set_barrier_extra(s, 1));
+  }
   {
     PhaseTimer pt(s, 3);
     if (s->opt.precision == LGDM_PREC_FP32_TANGENT)
@@ -875,6 +918,7 @@ lgdm_status run_krylov(lgdm_sim *s, int mode, SolveResult *out) {
       LGDM_CUDA(s, launch_bicgstab_grouped<double>(s->nd, s->d_kself, s->d_one, s->d_gstart, s->d_one + 1, 1,
                                                    s->krylov_blocks, mode, s->stream));
   }
+  if (inject) LGDM_CUDA(s, set_barrier_extra(s, 0));
   return finish_launch(s, mode, out);
 }
 
@@ -1008,6 +1052,42 @@ lgdm_status lgdm_commit(lgdm_sim *s) {
   } else {
     LGDM_CUDA(s, cudaMemsetAsync(s->reaction, 0, sizeof(double), s->stream));
   }
+  s->load_commit = s->load_trial;
+  if (!s->substep_commits) {
+    // external work (R17): trapezoid rule from the previous point of the curve
+    LGDM_CUDA(s, launch_external_work(s->reaction, s->load_commit - s->load_point, s->stream));
+    s->counters[0] += 1;
+    s->load_point = s->load_commit;
+  }
+  return LGDM_OK;
+}
+
+lgdm_status lgdm_get_committed(lgdm_sim *s, double *load, double *external_work, double *reaction) {
+  if (!s) return fail(nullptr, LGDM_ERR_INVALID_ARG, "NULL handle");
+  double v[3] = {0.0, 0.0, 0.0};
+  LGDM_CUDA(s, cudaMemcpyAsync(v, s->reaction, 3 * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+  LGDM_CUDA(s, cudaStreamSynchronize(s->stream));
+  if (load) *load = s->load_commit;
+  if (external_work) *external_work = v[1];
+  if (reaction) *reaction = v[0];
+  return LGDM_OK;
+}
+
+lgdm_status lgdm_set_committed(lgdm_sim *s, double load, double external_work, double reaction) {
+  if (!s) return fail(nullptr, LGDM_ERR_INVALID_ARG, "NULL handle");
+  if (!std::isfinite(load) || !std::isfinite(external_work) || !std::isfinite(reaction))
+    return fail(s, LGDM_ERR_NONFINITE, "committed scalars must be finite");
+  const double v[3] = {reaction, external_work, reaction};
+  LGDM_CUDA(s, cudaMemcpyAsync(s->reaction, v, 3 * sizeof(double), cudaMemcpyHostToDevice, s->stream));
+  LGDM_CUDA(s, cudaStreamSynchronize(s->stream));
+  s->load_commit = s->load_trial = s->load_point = load;
+  return LGDM_OK;
+}
+
+lgdm_status lgdm_inject_fault(lgdm_sim *s, int32_t kind) {
+  if (!s) return fail(nullptr, LGDM_ERR_INVALID_ARG, "NULL handle");
+  if (kind < 0 || kind > 2) return fail(s, LGDM_ERR_INVALID_ARG, "unknown fault kind");
+  s->fault = kind;
   return LGDM_OK;
 }
 
@@ -1070,6 +1150,33 @@ lgdm_status lgdm_get_energy(lgdm_sim *s, double *psi) {
   return LGDM_OK;
 }
 
+lgdm_status lgdm_get_dissipated_energy(lgdm_sim *s, double *dissipated, double *psi) {
+  if (!s || !dissipated) return fail(s, LGDM_ERR_INVALID_ARG, "NULL argument");
+  double e = 0.0, w = 0.0;
+  lgdm_status st = lgdm_get_energy(s, &e);
+  if (st != LGDM_OK) return st;
+  st = lgdm_get_committed(s, nullptr, &w, nullptr);
+  if (st != LGDM_OK) return st;
+  *dissipated = w - e;
+  if (psi) *psi = e;
+  return LGDM_OK;
+}
+
+lgdm_status lgdm_get_damaged_volume(lgdm_sim *s, double threshold, double *volume) {
+  if (!s || !volume) return fail(s, LGDM_ERR_INVALID_ARG, "NULL argument");
+  if (!std::isfinite(threshold)) return fail(s, LGDM_ERR_INVALID_ARG, "threshold must be finite");
+  const int64_t nblk = ((int64_t)s->nel * s->ngp + 4095) / 4096;
+  LGDM_CUDA(s, launch_damaged_volume(s->elem, s->mesh_view(), s->mc, s->kappa_hist, threshold, s->re, s->field_tmp,
+                                     s->field_tmp + nblk + 1, s->stream));
+  double v = 0.0;
+  LGDM_CUDA(s, cudaMemcpyAsync(&v, s->field_tmp + nblk + 1, sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+  LGDM_CUDA(s, cudaStreamSynchronize(s->stream));
+  s->counters[0] += 3;
+  s->assembled = false;
+  *volume = v;
+  return LGDM_OK;
+}
+
 lgdm_status lgdm_get_reaction(lgdm_sim *s, double *reaction) {
   if (!s || !reaction) return fail(s, LGDM_ERR_INVALID_ARG, "NULL argument");
   LGDM_CUDA(s, cudaMemcpyAsync(reaction, s->reaction, sizeof(double), cudaMemcpyDeviceToHost, s->stream));
@@ -1105,11 +1212,7 @@ lgdm_status advance(lgdm_sim *s, double from, double to, int depth, int32_t *ite
   bool done = false;
   lgdm_status st = attempt(s, to, &done, iters);
   if (st != LGDM_OK) return st;
-  if (done) {
-    st = lgdm_commit(s);
-    if (st == LGDM_OK) s->load_commit = to;
-    return st;
-  }
+  if (done) return lgdm_commit(s);
   if (depth >= s->opt.max_halvings) {
     LGDM_CUDA(s, cudaMemcpyAsync(s->u, s->u_commit, sizeof(double) * s->ndof, cudaMemcpyDeviceToDevice, s->stream));
     return fail(s, LGDM_ERR_NOT_CONVERGED,
@@ -1123,12 +1226,26 @@ lgdm_status advance(lgdm_sim *s, double from, double to, int depth, int32_t *ite
   return advance(s, mid, to, depth + 1, iters);
 }
 
+// A load step driven by the library, halvings included, is one point of the
+// load-reaction curve: the commits of its sub-steps add no external work, the
+// end point adds the trapezoid from the previous point.
+lgdm_status advance_step(lgdm_sim *s, double from, double to, int depth, int32_t *iters) {
+  s->substep_commits = true;
+  lgdm_status st = advance(s, from, to, depth, iters);
+  s->substep_commits = false;
+  if (st != LGDM_OK) return st;
+  LGDM_CUDA(s, launch_external_work(s->reaction, s->load_commit - s->load_point, s->stream));
+  s->counters[0] += 1;
+  s->load_point = s->load_commit;
+  return LGDM_OK;
+}
+
 }  // namespace
 
 extern "C" lgdm_status lgdm_run_step(lgdm_sim *s, double load, int32_t *newton_iters) {
   if (!s) return fail(nullptr, LGDM_ERR_INVALID_ARG, "NULL handle");
   int32_t its = 0;
-  lgdm_status st = advance(s, s->load_commit, load, 0, &its);
+  lgdm_status st = advance_step(s, s->load_commit, load, 0, &its);
   if (newton_iters) *newton_iters = its;
   return st;
 }
@@ -1700,7 +1817,6 @@ lgdm_status lgdm_batch_run_step(lgdm_batch *b, const double *loads, int32_t *new
       if (conv[i] == 1) {
         st = lgdm_commit(b->sims[i]);
         if (st != LGDM_OK) return bfail(b, st, b->sims[i]->err);
-        b->sims[i]->load_commit = loads[i];
         act[i] = 0;
         todo[i] = 0;
       } else if (conv[i] == -1) {
@@ -1718,8 +1834,14 @@ lgdm_status lgdm_batch_run_step(lgdm_batch *b, const double *loads, int32_t *new
     if (s->opt.max_halvings > 0) {
       const double from = s->load_commit, mid = 0.5 * (from + loads[i]);
       s->counters[5] += 1;
+      s->substep_commits = true;
       st = advance(s, from, mid, 1, &extra);
       if (st == LGDM_OK) st = advance(s, mid, loads[i], 1, &extra);
+      s->substep_commits = false;
+      if (st == LGDM_OK) {                          // the halved step is one point of the curve
+        LGDM_BCUDA(b, launch_external_work(s->reaction, s->load_commit - s->load_point, s->stream));
+        s->load_point = s->load_commit;
+      }
     }
     its[i] += extra;
     if (status) status[i] = st;

@@ -782,6 +782,73 @@ cudaError_t launch_reaction_sum(const double *re, const int32_t *idx, const doub
   return cudaGetLastError();
 }
 
+__global__ void external_work_kernel(double *c, double dload) {
+  c[1] += 0.5 * (c[0] + c[2]) * dload;
+  c[2] = c[0];
+}
+cudaError_t launch_external_work(double *c, double dload, cudaStream_t s) {
+  external_work_kernel<<<1, 1, 0, s>>>(c, dload);
+  return cudaGetLastError();
+}
+
+// det J at Gauss point q of element e (unit weights of the 2-point rule).
+template <int ELEM>
+__device__ __forceinline__ double gp_det(const MeshView &m, int64_t e, int q) {
+  constexpr int DIM = Elem<ELEM>::DIM, NEN = Elem<ELEM>::NEN;
+  double J[DIM][DIM];
+#pragma unroll
+  for (int i = 0; i < DIM; ++i)
+#pragma unroll
+    for (int j = 0; j < DIM; ++j) J[i][j] = 0.0;
+#pragma unroll
+  for (int b = 0; b < NEN; ++b) {
+    const int32_t node = m.conn[e * NEN + b];
+    const double X[3] = {m.x[node], DIM > 1 ? m.y[node] : 0.0, DIM > 2 ? m.z[node] : 0.0};
+#pragma unroll
+    for (int i = 0; i < DIM; ++i)
+#pragma unroll
+      for (int j = 0; j < DIM; ++j) J[i][j] += X[i] * shape_dN<DIM>(q, b, j);
+  }
+  if constexpr (DIM == 1) return J[0][0];
+  else if constexpr (DIM == 2) return J[0][0] * J[1][1] - J[0][1] * J[1][0];
+  else
+    return J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) + J[0][1] * (J[1][2] * J[2][0] - J[1][0] * J[2][2]) +
+           J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
+}
+
+template <int ELEM>
+__global__ void damaged_volume_kernel(MeshView m, MatConst mc, const double *__restrict__ kh, double thr,
+                                      double *__restrict__ vol) {
+  constexpr int NEN = Elem<ELEM>::NEN;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)m.nel * NEN) return;
+  const int64_t e = t / NEN;
+  const double k = kh[t];
+  double D = 0.0;
+  if (k > mc.kappa0) D = 1.0 - mc.kappa0 / k * (1.0 - mc.alpha + mc.alpha * exp(-mc.beta * (k - mc.kappa0)));
+  vol[t] = (D > thr) ? gp_det<ELEM>(m, e, (int)(t % NEN)) * m.vol_scale[e] : 0.0;
+}
+
+cudaError_t launch_damaged_volume(int elem, const MeshView &m, const MatConst &mc, const double *kh, double thr,
+                                  double *vol, double *part, double *out, cudaStream_t s) {
+  const int nen = (elem == LGDM_L2) ? 2 : (elem == LGDM_Q4) ? 4 : 8;
+  const int64_t n = (int64_t)m.nel * nen;
+  const int grid = (int)((n + 255) / 256);
+  switch (elem) {
+    case LGDM_L2: damaged_volume_kernel<LGDM_L2><<<grid, 256, 0, s>>>(m, mc, kh, thr, vol); break;
+    case LGDM_Q4: damaged_volume_kernel<LGDM_Q4><<<grid, 256, 0, s>>>(m, mc, kh, thr, vol); break;
+    case LGDM_H8: damaged_volume_kernel<LGDM_H8><<<grid, 256, 0, s>>>(m, mc, kh, thr, vol); break;
+    default: return cudaErrorInvalidValue;
+  }
+  cudaError_t err = cudaGetLastError();
+  if (err != cudaSuccess) return err;
+  const int64_t chunk = 4096;
+  const int nblk = (int)((n + chunk - 1) / chunk);
+  chunk_sum_kernel<<<nblk, 256, 0, s>>>(vol, n, chunk, part);
+  chunk_sum_kernel<<<1, 256, 0, s>>>(part, nblk, nblk, out);
+  return cudaGetLastError();
+}
+
 // ------------------------------------------------------------------ batched kernels
 // Many simulations of one element type in one launch.  The members' element
 // tiles (pairs, nodes) are numbered consecutively; a block finds its member

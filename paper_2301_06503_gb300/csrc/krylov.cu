@@ -21,7 +21,6 @@
 namespace lgdm {
 
 constexpr int KT = KRYLOV_THREADS;
-constexpr unsigned long long BARRIER_NS = 2000000000ull;   // 2 s
 constexpr int KRYLOV_MAX_RESTARTS = 8;
 
 __device__ __forceinline__ unsigned long long globaltimer() {
@@ -30,8 +29,10 @@ __device__ __forceinline__ unsigned long long globaltimer() {
   return t;
 }
 
-// Returns false when the wait timed out (another block never arrived).
-__device__ bool grid_barrier(unsigned int *count, unsigned int *gen, unsigned int nblocks) {
+// Returns false when the wait timed out (another block never arrived within
+// limit_ns nanoseconds of this block's arrival).
+__device__ bool grid_barrier(unsigned int *count, unsigned int *gen, unsigned int nblocks,
+                             unsigned long long limit_ns) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -47,7 +48,7 @@ __device__ bool grid_barrier(unsigned int *count, unsigned int *gen, unsigned in
       const unsigned long long t0 = globaltimer();
       unsigned int spins = 0;
       while (g.load(cuda::memory_order_acquire) == my_gen) {
-        if ((++spins & 255u) == 0 && globaltimer() - t0 > BARRIER_NS) { ok = 0; break; }
+        if ((++spins & 255u) == 0 && globaltimer() - t0 > limit_ns) { ok = 0; break; }
       }
     }
     s_ok = ok;
@@ -204,6 +205,7 @@ __device__ __forceinline__ void bicgstab_body(const KrylovArgs &A, const int nb,
   __shared__ double ws[4 * KRYLOV_MAXW];
   const int T = A.tile;
   const int64_t NT = A.ntiles;
+  const unsigned int nbar = (unsigned int)(nb + A.barrier_extra);   // blocks each grid barrier waits for
   const int64_t t0 = (int64_t)bid * NT / nb, t1 = (int64_t)(bid + 1) * NT / nb;
   const int64_t n0 = min(t0 * T, (int64_t)A.nnode), n1 = min(t1 * T, (int64_t)A.nnode);
   const TT *vals = static_cast<const TT *>(A.vals);
@@ -230,7 +232,7 @@ __device__ __forceinline__ void bicgstab_body(const KrylovArgs &A, const int nb,
         lv[0] += b * b;
       }
     });
-    ok = grid_barrier(A.bar_count, A.bar_gen, nb);
+    ok = grid_barrier(A.bar_count, A.bar_gen, nbar, A.wait_ns);
     if (ok) {
       bnorm = sqrt(grid_sum(part(2, 0), NT));
       if (!(bnorm > 0.0)) status = isfinite(bnorm) ? 0 : 3;
@@ -245,7 +247,7 @@ __device__ __forceinline__ void bicgstab_body(const KrylovArgs &A, const int nb,
 #pragma unroll
             for (int i = 0; i < ND; ++i) A.ph[ND * a + i] = A.x[ND * a + i];
           }
-          if (!(ok = grid_barrier(A.bar_count, A.bar_gen, nb))) break;
+          if (!(ok = grid_barrier(A.bar_count, A.bar_gen, nbar, A.wait_ns))) break;
         }
         LGDM_REDUCE(1, 2, 0) {
           double y[ND];
@@ -261,7 +263,7 @@ __device__ __forceinline__ void bicgstab_body(const KrylovArgs &A, const int nb,
             lv[0] += rn * rn;
           }
         });
-        if (!(ok = grid_barrier(A.bar_count, A.bar_gen, nb))) break;
+        if (!(ok = grid_barrier(A.bar_count, A.bar_gen, nbar, A.wait_ns))) break;
         rho = grid_sum(part(2, 0), NT);
         rel = sqrt(rho) / bnorm;
         if (!isfinite(rho)) { status = 3; break; }
@@ -296,7 +298,7 @@ __device__ __forceinline__ void bicgstab_body(const KrylovArgs &A, const int nb,
 #pragma unroll
         for (int i = 0; i < ND; ++i) A.ph[ND * a + i] = ph[i];
       }
-      if (!(ok = grid_barrier(A.bar_count, A.bar_gen, nb))) break;
+      if (!(ok = grid_barrier(A.bar_count, A.bar_gen, nbar, A.wait_ns))) break;
       LGDM_REDUCE(1, 0, 0) {
         double y[ND];
         spmv_node<ND, TT>(A.p, vals, A.ph, a, y);
@@ -306,7 +308,7 @@ __device__ __forceinline__ void bicgstab_body(const KrylovArgs &A, const int nb,
           lv[0] += A.r0[ND * a + i] * y[i];
         }
       });
-      if (!(ok = grid_barrier(A.bar_count, A.bar_gen, nb))) break;
+      if (!(ok = grid_barrier(A.bar_count, A.bar_gen, nbar, A.wait_ns))) break;
       const double r0v = grid_sum(part(0, 0), NT);
       if (!isfinite(r0v)) { status = 3; break; }
       if (r0v == 0.0) {                         // breakdown: restart from x
@@ -329,7 +331,7 @@ __device__ __forceinline__ void bicgstab_body(const KrylovArgs &A, const int nb,
 #pragma unroll
         for (int i = 0; i < ND; ++i) A.sh[ND * a + i] = sh[i];
       }
-      if (!(ok = grid_barrier(A.bar_count, A.bar_gen, nb))) break;
+      if (!(ok = grid_barrier(A.bar_count, A.bar_gen, nbar, A.wait_ns))) break;
       LGDM_REDUCE(2, 1, 0) {
         double y[ND];
         spmv_node<ND, TT>(A.p, vals, A.sh, a, y);
@@ -340,7 +342,7 @@ __device__ __forceinline__ void bicgstab_body(const KrylovArgs &A, const int nb,
           lv[1] += y[i] * y[i];
         }
       });
-      if (!(ok = grid_barrier(A.bar_count, A.bar_gen, nb))) break;
+      if (!(ok = grid_barrier(A.bar_count, A.bar_gen, nbar, A.wait_ns))) break;
       const double ts = grid_sum(part(1, 0), NT), tt = grid_sum(part(1, 1), NT);
       omega = (tt > 0.0) ? ts / tt : 0.0;
       LGDM_REDUCE(2, 2, 0) {
@@ -354,7 +356,7 @@ __device__ __forceinline__ void bicgstab_body(const KrylovArgs &A, const int nb,
           lv[1] += A.r0[row] * rn;
         }
       });
-      if (!(ok = grid_barrier(A.bar_count, A.bar_gen, nb))) break;
+      if (!(ok = grid_barrier(A.bar_count, A.bar_gen, nbar, A.wait_ns))) break;
       const double rr = grid_sum(part(2, 0), NT);
       rho_old = rho;
       rho = grid_sum(part(2, 1), NT);
@@ -406,7 +408,7 @@ __device__ __forceinline__ void bicgstab_body(const KrylovArgs &A, const int nb,
         }
       }
     });
-    ok = grid_barrier(A.bar_count, A.bar_gen, nb);
+    ok = grid_barrier(A.bar_count, A.bar_gen, nbar, A.wait_ns);
     if (ok) {
       double nrm[4];
 #pragma unroll
@@ -469,9 +471,11 @@ __global__ void __launch_bounds__(KT) bicgstab_grouped_kernel(const KrylovArgs *
   bicgstab_body<ND, TT>(A, group_start[lo + 1] - group_start[lo], b - group_start[lo], mode);
 }
 
-// Zero the barrier words and the status of every active member before a grouped launch.
+// Zero the barrier words and the status of every active member before a
+// grouped launch; a solve (mode != 2) also clears the previous result, which
+// the update launch (mode 2) still reads.
 __global__ void reset_members_kernel(const KrylovArgs *__restrict__ args, const int32_t *__restrict__ members,
-                                     const int32_t *__restrict__ active, int n) {
+                                     const int32_t *__restrict__ active, int n, int mode) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const int sm = members[i];
@@ -479,6 +483,11 @@ __global__ void reset_members_kernel(const KrylovArgs *__restrict__ args, const 
   args[sm].bar_count[0] = 0u;
   args[sm].bar_gen[0] = 0u;
   args[sm].res->status = 0;
+  if (mode != 2) {
+    args[sm].res->iters = 0;
+    args[sm].res->rel_res = 0.0;
+    args[sm].res->bnorm = 0.0;
+  }
 }
 
 // Copy every member's result block into one array (one copy to the host).
@@ -496,7 +505,7 @@ template <typename TT>
 cudaError_t launch_bicgstab_grouped(int nd, const KrylovArgs *d_args, const int32_t *d_members,
                                     const int32_t *d_group_start, const int32_t *d_active, int nsys,
                                     int total_blocks, int mode, cudaStream_t s) {
-  reset_members_kernel<<<(nsys + 127) / 128, 128, 0, s>>>(d_args, d_members, d_active, nsys);
+  reset_members_kernel<<<(nsys + 127) / 128, 128, 0, s>>>(d_args, d_members, d_active, nsys, mode);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   int ns = nsys;
@@ -596,6 +605,7 @@ __device__ void gm_residual(const KrylovArgs &A, const GmresArgs &G, int64_t r0,
 template <int ND, typename TT>
 __global__ void __launch_bounds__(KT) gmres_kernel(KrylovArgs A, GmresArgs G) {
   const int nb = gridDim.x, bid = blockIdx.x;
+  const unsigned int nbar = (unsigned int)(nb + A.barrier_extra);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   constexpr int NW = KT / 32;
   const int64_t n0 = (int64_t)bid * A.nnode / nb, n1 = (int64_t)(bid + 1) * A.nnode / nb;
@@ -629,7 +639,7 @@ __global__ void __launch_bounds__(KT) gmres_kernel(KrylovArgs A, GmresArgs G) {
     for (int64_t row = r0 + threadIdx.x; row < r1; row += KT) l += A.rhs[row] * A.rhs[row];
     publish(0, l);
     for (int64_t row = r0 + threadIdx.x; row < r1; row += KT) G.xs[row] = A.x[row];
-    ok = grid_barrier(A.bar_count, A.bar_gen, nb);
+    ok = grid_barrier(A.bar_count, A.bar_gen, nbar, A.wait_ns);
     if (ok) bnorm = sqrt(grid_sum(part(0), nb));
   }
   if (ok && !(bnorm > 0.0)) status = isfinite(bnorm) ? 0 : 3;
@@ -639,7 +649,7 @@ __global__ void __launch_bounds__(KT) gmres_kernel(KrylovArgs A, GmresArgs G) {
     double l;
     gm_residual<ND, TT>(A, G, r0, r1, V, &l);            // V_0 <- r (unnormalised)
     publish(0, l);
-    if (!(ok = grid_barrier(A.bar_count, A.bar_gen, nb))) break;
+    if (!(ok = grid_barrier(A.bar_count, A.bar_gen, nbar, A.wait_ns))) break;
     const double beta = sqrt(grid_sum(part(0), nb));
     rel = beta / bnorm;
     if (!isfinite(beta)) { status = 3; break; }
@@ -677,7 +687,7 @@ __global__ void __launch_bounds__(KT) gmres_kernel(KrylovArgs A, GmresArgs G) {
         for (int q = 0; q < ND; ++q) s += (double)mm[q] * Vj[a * ND + q];
         G.xs[row] = s;
       }
-      if (!(ok = grid_barrier(A.bar_count, A.bar_gen, nb))) break;
+      if (!(ok = grid_barrier(A.bar_count, A.bar_gen, nbar, A.wait_ns))) break;
       for (int64_t row = r0 + threadIdx.x; row < r1; row += KT)
         W[row] = spmv_row<ND, TT>(A.p, static_cast<const TT *>(A.vals), G.xs, row);
       __syncthreads();
@@ -690,9 +700,9 @@ __global__ void __launch_bounds__(KT) gmres_kernel(KrylovArgs A, GmresArgs G) {
         for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
         if (lane == 0) __stcg(part(i) + bid, s);
       }
-      if (!(ok = grid_barrier(A.bar_count, A.bar_gen, nb))) break;
+      if (!(ok = grid_barrier(A.bar_count, A.bar_gen, nbar, A.wait_ns))) break;
       reduce(j + 1);
-      if (!(ok = grid_barrier(A.bar_count, A.bar_gen, nb))) break;
+      if (!(ok = grid_barrier(A.bar_count, A.bar_gen, nbar, A.wait_ns))) break;
       for (int i = threadIdx.x; i <= j; i += KT) s_h[i] = __ldcg(G.final + i);
       __syncthreads();
       for (int64_t row = r0 + threadIdx.x; row < r1; row += KT) {
@@ -710,9 +720,9 @@ __global__ void __launch_bounds__(KT) gmres_kernel(KrylovArgs A, GmresArgs G) {
         for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
         if (lane == 0) __stcg(part(i) + bid, s);
       }
-      if (!(ok = grid_barrier(A.bar_count, A.bar_gen, nb))) break;
+      if (!(ok = grid_barrier(A.bar_count, A.bar_gen, nbar, A.wait_ns))) break;
       reduce(j + 1);
-      if (!(ok = grid_barrier(A.bar_count, A.bar_gen, nb))) break;
+      if (!(ok = grid_barrier(A.bar_count, A.bar_gen, nbar, A.wait_ns))) break;
       for (int i = threadIdx.x; i <= j; i += KT) s_h2[i] = __ldcg(G.final + i);
       __syncthreads();
       // ||w|| after both passes, computed directly (a Pythagorean update
@@ -726,7 +736,7 @@ __global__ void __launch_bounds__(KT) gmres_kernel(KrylovArgs A, GmresArgs G) {
         lw += wn * wn;
       }
       publish(GMRES_MAX_M + 1, lw);
-      if (!(ok = grid_barrier(A.bar_count, A.bar_gen, nb))) break;
+      if (!(ok = grid_barrier(A.bar_count, A.bar_gen, nbar, A.wait_ns))) break;
       const double hnext = sqrt(grid_sum(part(GMRES_MAX_M + 1), nb));
       for (int64_t row = r0 + threadIdx.x; row < r1; row += KT) W[row] = (hnext > 0.0) ? W[row] / hnext : 0.0;
       // Hessenberg column, previous rotations, new rotation (same in every block)
@@ -758,7 +768,7 @@ __global__ void __launch_bounds__(KT) gmres_kernel(KrylovArgs A, GmresArgs G) {
     }
     if (!ok || status == 3) break;
     // x += M^-1 V_k y with R y = g (back substitution in block 0)
-    if (!(ok = grid_barrier(A.bar_count, A.bar_gen, nb))) break;
+    if (!(ok = grid_barrier(A.bar_count, A.bar_gen, nbar, A.wait_ns))) break;
     if (bid == 0 && threadIdx.x == 0) {
       for (int i = k - 1; i >= 0; --i) {
         double s = s_g[i];
@@ -767,7 +777,7 @@ __global__ void __launch_bounds__(KT) gmres_kernel(KrylovArgs A, GmresArgs G) {
         G.y[i] = (d != 0.0) ? s / d : 0.0;
       }
     }
-    if (!(ok = grid_barrier(A.bar_count, A.bar_gen, nb))) break;
+    if (!(ok = grid_barrier(A.bar_count, A.bar_gen, nbar, A.wait_ns))) break;
     for (int64_t row = r0 + threadIdx.x; row < r1; row += KT) {
       double s = 0.0;
       for (int i = 0; i < k; ++i) s += __ldcg(G.y + i) * V[i * ld + row];
@@ -784,7 +794,7 @@ __global__ void __launch_bounds__(KT) gmres_kernel(KrylovArgs A, GmresArgs G) {
       A.x[row] += s;
       G.xs[row] = A.x[row];
     }
-    if (!(ok = grid_barrier(A.bar_count, A.bar_gen, nb))) break;
+    if (!(ok = grid_barrier(A.bar_count, A.bar_gen, nbar, A.wait_ns))) break;
   }
   if (!ok) {
     if (threadIdx.x == 0) atomicMax(&A.res->status, 4);

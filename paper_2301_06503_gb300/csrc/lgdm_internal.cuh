@@ -116,6 +116,13 @@ cudaError_t launch_damage_field(const MatConst &mc, const double *kappa_hist, in
                                 cudaStream_t s);
 cudaError_t launch_reaction_sum(const double *re, const int32_t *idx, const double *w, int32_t n,
                                 double *out, cudaStream_t s);
+// committed scalars c[0] reaction, c[1] external work, c[2] previous reaction:
+// c[1] += (c[0] + c[2]) dload / 2; c[2] = c[0]
+cudaError_t launch_external_work(double *c, double dload, cudaStream_t s);
+// volume of the Gauss points whose damage D(kappa_hist) exceeds threshold:
+// per-point dV (or 0) into vol [nel*ngp], fixed-order sum into *out
+cudaError_t launch_damaged_volume(int elem, const MeshView &m, const MatConst &mc, const double *kh,
+                                  double threshold, double *vol, double *part, double *out, cudaStream_t s);
 
 // One member of a batch, as the batched kernels see it.
 struct BatchSim {
@@ -185,6 +192,8 @@ struct KrylovArgs {
   double *partial;            // [3 slots][4 values][ntiles]
   unsigned int *bar_count, *bar_gen;
   SolveResult *res;
+  unsigned long long wait_ns;  // limit of each grid-barrier wait
+  int32_t barrier_extra;       // blocks the barrier waits for beyond those launched (failure injection; 0)
 };
 // mode 0: solve; 1: solve, u += delta, Newton test; 2: update and test only.
 template <typename TT>

@@ -7,11 +7,14 @@
 // file-scope __device__ array instead of a workspace: the caller passes only
 // the system (inputs) and the solution buffer (output).
 //
-// The array is reserved when the library is loaded, on every GPU that loads
-// it, and stays reserved until the process exits.  Host code cannot use the
-// array's name as a device address; at the first call on a device, with that
-// device current, its address is fetched once with cudaGetSymbolAddress and
-// cached per device.
+// CUDA loads the library's device code lazily, and this file's module holds
+// only the array: the array is reserved on a device by the first call there,
+// when its address is fetched with cudaGetSymbolAddress (with that device
+// current; the address is cached per device), and it stays reserved until
+// the process exits.  A call with nnode == 0 does only this set-up, so a
+// caller can make it before reserving the rest of the device memory.  Host
+// code cannot use the array's name as a device address: it only ever passes
+// the fetched address to the kernels.
 #include "lgdm_internal.cuh"
 
 #include <algorithm>
@@ -43,7 +46,8 @@ using namespace lgdm;
 extern "C" lgdm_status lgdm_solve_noalloc(int32_t nd, int32_t nnode, const int32_t *nbr_ptr, const int32_t *nbr,
                                           const double *vals, const double *rhs, double *x, double rtol,
                                           int32_t max_iter, void *stream, int32_t *iters, double *rel_res) {
-  if (nd < 2 || nd > 4 || nnode <= 0 || !nbr_ptr || !nbr || !vals || !rhs || !x || !(rtol > 0.0) || max_iter < 1)
+  if (nnode < 0 || (nnode > 0 && (nd < 2 || nd > 4 || !nbr_ptr || !nbr || !vals || !rhs || !x || !(rtol > 0.0) ||
+                                   max_iter < 1)))
     return err(LGDM_ERR_INVALID_ARG, "bad argument");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   int dev = 0;
@@ -55,11 +59,18 @@ extern "C" lgdm_status lgdm_solve_noalloc(int32_t nd, int32_t nnode, const int32
     if (!g_addr[dev]) {
       void *p = nullptr;
       const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+      if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        return err(LGDM_ERR_OOM, "the 64 MiB static scratch array could not be reserved on device " +
+                                     std::to_string(dev) + " (device memory exhausted): make a first call "
+                                     "(nnode = 0 suffices) before reserving the device memory");
+      }
       if (e != cudaSuccess) return err(LGDM_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
       g_addr[dev] = p;
     }
     base = g_addr[dev];
   }
+  if (nnode == 0) return LGDM_OK;                  // set-up only
   const int nblocks_max = bicgstab_max_blocks<double>();
   const int64_t ndof = (int64_t)nd * nnode;
   const int64_t ntiles = krylov_ntiles(nnode);
@@ -124,15 +135,18 @@ extern "C" lgdm_status lgdm_solve_noalloc(int32_t nd, int32_t nnode, const int32
   a.bar_count = bar;
   a.bar_gen = bar + 1;
   a.res = res;
-  e = launch_bicgstab<double>(a, nb, 0, s);
+  a.wait_ns = 2000000000ull;                       // 2 s per grid-barrier wait
+  a.barrier_extra = 0;
+  e = cudaMemsetAsync(res, 0, sizeof(SolveResult), s);   // no stale result survives a timed-out launch
+  if (e == cudaSuccess) e = launch_bicgstab<double>(a, nb, 0, s);
   if (e != cudaSuccess) return err(LGDM_ERR_CUDA, std::string("launch: ") + cudaGetErrorString(e));
   SolveResult out{};
   e = cudaMemcpyAsync(&out, res, sizeof(SolveResult), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return err(LGDM_ERR_CUDA, std::string("sync: ") + cudaGetErrorString(e));
+  if (out.status == 4) return err(LGDM_ERR_TIMEOUT, "grid barrier timed out");
   if (iters) *iters = out.iters;
   if (rel_res) *rel_res = out.rel_res;
-  if (out.status == 4) return err(LGDM_ERR_TIMEOUT, "grid barrier timed out");
   if (out.status == 3) return err(LGDM_ERR_NONFINITE, "non-finite value in the solve");
   return LGDM_OK;
 }

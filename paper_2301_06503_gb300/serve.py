@@ -7,17 +7,24 @@ over time.  Each scheduler tick:
    (the sum of the resident simulations' workspaces) and the slot count
    allow; an admitted simulation keeps its mesh, CSR pattern and history
    resident until it finishes;
-2. advances every resident simulation by one load step together: a batch
-   over the residents runs the Newton iterations of all of them in the same
-   launches (persistent element kernel, grouped solves), each simulation at
-   its own load value;
-3. retires the simulations whose last load step is done (their slot and
-   memory are reused by the next admission).
+2. runs ONE batched Newton iteration for every resident simulation: each
+   resident that is not inside a load step begins its next one, then a batch
+   over all residents assembles, solves and updates them in the same launches
+   (persistent element kernel, grouped solves), each at its own load value;
+3. commits every resident whose Newton test passed (the library keeps its
+   reaction, external work and history), and hands a resident that used up
+   its Newton iterations to the library's own load-step driver (increment
+   halving from its committed state);
+4. retires the simulations whose last load step is done; their slots and
+   memory go to the next admission.
 
-A request's result is bitwise the same whether it ran alone or among others
-(the batch guarantees it), so serving changes only latency and throughput.
-The scheduler is host code; all arithmetic of the method runs in the
-library's kernels.
+New requests therefore join between Newton iterations, not between load
+steps.  The batch is rebuilt when the membership changes (its descriptors and
+launch sizes depend on the members); the autotuned tile sizes are kept.  A
+request's result is bitwise the same whether it ran alone or among others (a
+batch member computes exactly what it computes alone), so serving changes
+only latency and throughput.  The scheduler is host code; all arithmetic of
+the method runs in the library's kernels.
 """
 import time
 from dataclasses import dataclass, field
@@ -45,7 +52,12 @@ class Job:
     newton_iters: int = 0
     krylov_iters: int = 0
     psi: Optional[float] = None             # stored energy (Eq. 1) at the last committed state
+    dissipated: Optional[float] = None      # external work minus stored energy, from the library
+    external_work: Optional[float] = None
+    damage: Optional[np.ndarray] = None     # final committed damage field (kept on request)
     status: int = 0
+    in_step: bool = False                   # inside a load step (Newton iterations running)
+    step_iters: int = 0                     # Newton iterations of the current load step
 
     @property
     def time_to_solution(self):
@@ -56,22 +68,23 @@ class Job:
         return None if self.finish is None else self.finish - self.admit
 
     def record(self) -> dict:
-        """One line of the per-request log: times, iteration counts, peak load
-        and dissipated energy (external work by the trapezoid rule over the
-        served load steps minus the stored energy)."""
-        loads = [0.0] + [self.problem.load(n) for n in range(1, len(self.reactions) + 1)]
-        reac = [0.0] + list(self.reactions)
-        w_ext = sum(0.5 * (reac[k] + reac[k - 1]) * (loads[k] - loads[k - 1]) for k in range(1, len(reac)))
+        """One line of the per-request log: times, iteration counts, peak load,
+        external work and dissipated energy (both kept by the library at every
+        commit)."""
         return {"rid": self.rid, "arrival": self.arrival, "admit": self.admit, "finish": self.finish,
                 "status": self.status, "load_steps": self.step, "newton_iters": self.newton_iters,
                 "krylov_iters": self.krylov_iters,
                 "peak_load": max(self.reactions) if self.reactions else None,
-                "dissipated_energy": (w_ext - self.psi) if self.psi is not None else None}
+                "external_work": self.external_work, "stored_energy": self.psi,
+                "dissipated_energy": self.dissipated}
 
 
 class Server:
     def __init__(self, budget_bytes: int, max_resident: int = 64, precision: str = "fp32",
-                 stream: Optional[torch.cuda.Stream] = None, autotune: bool = True, log=None, **sim_opts):
+                 stream: Optional[torch.cuda.Stream] = None, autotune: bool = True, log=None,
+                 keep_fields: bool = False, **sim_opts):
+        self.keep_fields = keep_fields
+        self.max_newton = int(sim_opts.get("max_newton", 50))
         self.budget = int(budget_bytes)
         self.max_resident = max_resident
         self.precision = precision
@@ -85,6 +98,7 @@ class Server:
         self.peak_used = 0
         self.batch: Optional[Batch] = None
         self.ticks = 0
+        self.rebuilds = 0
         self.tuning = None
         self.log = log
         self._t0 = time.perf_counter()
@@ -119,7 +133,10 @@ class Server:
                 job.finish = now
                 job.krylov_iters = job.sim.counters()["krylov_iters"]
                 if job.status == 0:
-                    job.psi = job.sim.energy()
+                    job.dissipated, job.psi = job.sim.dissipated_energy()
+                    job.external_work = job.sim.committed()[1]
+                    if self.keep_fields:
+                        job.damage = job.sim.field("damage")
                 job.sim.close()
                 job.sim = None
                 self.used -= job.bytes
@@ -134,6 +151,7 @@ class Server:
         if self.batch is not None:
             self.batch.close()
             self.batch = None
+        self.rebuilds += 1
         if self.resident:
             self.batch = Batch([j.sim for j in self.resident])
             if self.autotune and self.tuning is None:
@@ -144,23 +162,43 @@ class Server:
                 self.batch.set_tuning(self.tuning["block_threads"], self.tuning["grid_factor"], True)
 
     # ------------------------------------------------------------------ ticks
+    def _finish_step(self, j: Job):
+        j.step += 1
+        j.in_step = False
+        j.reactions.append(j.sim.reaction())
+
     def tick(self, now: float):
+        """Admit, one batched Newton iteration of every resident, commit, retire."""
+        from ._lib import LgdmError
         changed = self._admit(now)
         if changed or (self.batch is None and self.resident):
             self._rebuild()
         if not self.resident:
             return
-        loads = [j.problem.load(j.step + 1) for j in self.resident]
-        its, status = self.batch.run_step(loads)
-        for j, it, st in zip(self.resident, its, status):
-            j.newton_iters += int(it)
-            j.status = int(st)
-            j.step += 1
-            j.reactions.append(j.sim.reaction())
+        for j in self.resident:
+            if not j.in_step:
+                j.sim.begin_step(j.problem.load(j.step + 1))
+                j.in_step = True
+                j.step_iters = 0
+        conv, kits = self.batch.newton_step()
+        for j, c, kit in zip(self.resident, conv, kits):
+            j.step_iters += 1
+            j.newton_iters += 1
+            if c == 1:
+                j.sim.commit()
+                self._finish_step(j)
+            elif c == -1 or j.step_iters >= self.max_newton:
+                # diverged or out of Newton iterations: the library's load-step
+                # driver halves the increment from the committed state
+                try:
+                    j.newton_iters += j.sim.run_step(j.problem.load(j.step + 1))
+                    self._finish_step(j)
+                except LgdmError as e:
+                    j.status = int(e.status)
         self.ticks += 1
         if self.log is not None:
             self.log(f"tick {self.ticks} t={self._clock():.2f}s resident={len(self.resident)} "
-                     f"queued={len(self.queue)} done={len(self.done)} newton={list(map(int, its))}")
+                     f"queued={len(self.queue)} done={len(self.done)} steps={[j.step for j in self.resident]}")
         if self._retire(self._clock()):
             self._rebuild()
 
@@ -196,7 +234,8 @@ class Server:
             "p99_time_to_solution_s": float(np.percentile(tts, 99)) if ok else None,
             "p50_service_s": float(np.percentile(svc, 50)) if ok else None,
             "p99_service_s": float(np.percentile(svc, 99)) if ok else None,
-            "ticks": self.ticks, "peak_resident_bytes": self.peak_used, "budget_bytes": self.budget,
+            "ticks": self.ticks, "batch_rebuilds": self.rebuilds, "peak_resident_bytes": self.peak_used,
+            "budget_bytes": self.budget,
         }
 
     def records(self) -> List[dict]:
@@ -224,6 +263,10 @@ def run_one_at_a_time(jobs: List[Job], precision: str = "fp64", stream=None, **s
                 break
             job.reactions.append(s.reaction())
             job.step = n
+        if job.status == 0:
+            job.dissipated, job.psi = s.dissipated_energy()
+            job.external_work = s.committed()[1]
+        job.krylov_iters = s.counters()["krylov_iters"]
         s.close()
         job.finish = time.perf_counter() - t0
     wall = time.perf_counter() - t0

@@ -30,7 +30,8 @@ def _p(a, ct):
 
 
 def make_options(precision="fp64", precond="block", newton_tol=1e-8, krylov_rtol=None, max_newton=50,
-                 max_krylov=5000, max_halvings=6, krylov_blocks=0, gmres_m=64, krylov="bicgstab"):
+                 max_krylov=5000, max_halvings=6, krylov_blocks=0, gmres_m=64, krylov="bicgstab",
+                 wait_limit_s=2.0):
     o = L.Options()
     L.check(L.load().lgdm_default_options(C.byref(o)))
     o.precision = _PREC[precision]
@@ -43,6 +44,7 @@ def make_options(precision="fp64", precond="block", newton_tol=1e-8, krylov_rtol
     o.krylov_blocks = krylov_blocks
     o.gmres_m = gmres_m
     o.krylov_method = {"bicgstab": 0, "gmres": 1}[krylov]
+    o.wait_limit_s = wait_limit_s
     return o
 
 
@@ -225,10 +227,67 @@ class Sim:
         self._ck(self._lib.lgdm_get_energy(self.h, C.byref(e)))
         return float(e.value)
 
-    def run(self, loads):
-        """Run the given load values in order; returns (reactions, newton_iters)."""
+    def committed(self):
+        """(load, external work, reaction) of the committed state."""
+        ld, w, r = C.c_double(), C.c_double(), C.c_double()
+        self._ck(self._lib.lgdm_get_committed(self.h, C.byref(ld), C.byref(w), C.byref(r)))
+        return float(ld.value), float(w.value), float(r.value)
+
+    def set_committed(self, load, external_work, reaction):
+        self._ck(self._lib.lgdm_set_committed(self.h, float(load), float(external_work), float(reaction)))
+
+    def checkpoint(self) -> dict:
+        """Everything a resumed run needs: dofs, history and committed scalars."""
+        load, w, r = self.committed()
+        return {"u": self.field("u"), "kappa_hist": self.field("kappa_hist"), "load": load,
+                "external_work": w, "reaction": r}
+
+    def restore(self, ck):
+        self.set_state(ck["u"], ck["kappa_hist"])
+        self.set_committed(ck["load"], ck["external_work"], ck["reaction"])
+
+    def dissipated_energy(self):
+        """(dissipated energy, stored energy) at the committed state."""
+        d, e = C.c_double(), C.c_double()
+        self._ck(self._lib.lgdm_get_dissipated_energy(self.h, C.byref(d), C.byref(e)))
+        return float(d.value), float(e.value)
+
+    def damaged_volume(self, threshold=0.9) -> float:
+        """Volume of the Gauss points whose committed damage exceeds threshold."""
+        v = C.c_double()
+        self._ck(self._lib.lgdm_get_damaged_volume(self.h, float(threshold), C.byref(v)))
+        return float(v.value)
+
+    def inject_fault(self, kind):
+        """Failure injection for tests: 1 barrier timeout, 2 NaN state, 0 none."""
+        self._ck(self._lib.lgdm_inject_fault(self.h, int(kind)))
+
+    def snapshot(self, path=None) -> dict:
+        """Fields of the committed state, headless: damage and history per Gauss
+        point, nodal displacement and micro-equivalent strain, with the load,
+        reaction and damaged (D > 0.9) volume; written to ``path`` (.npz) if given."""
+        load, w, r = self.committed()
+        snap = {"load": load, "reaction": r, "external_work": w, "damage": self.field("damage"),
+                "kappa_hist": self.field("kappa_hist"), "displacement": self.field("displacement"),
+                "ebar": self.field("ebar"), "damaged_volume_0.9": self.damaged_volume(0.9)}
+        if path is not None:
+            np.savez(path, **snap)
+        return snap
+
+    def run(self, loads, snapshot_at=(), snapshot_dir=None):
+        """Run the given load values in order; returns (reactions, newton_iters).
+        After each load in ``snapshot_at`` the committed fields are stored
+        (``self.snapshots[load]``, and snapshot_dir/snapshot_<load>.npz)."""
         reac, its = [], []
+        marks = {float(x) for x in snapshot_at}
+        self.snapshots = getattr(self, "snapshots", {})
         for lv in loads:
             its.append(self.run_step(lv))
             reac.append(self.reaction())
+            if float(lv) in marks:
+                path = None
+                if snapshot_dir is not None:
+                    import os
+                    path = os.path.join(snapshot_dir, f"snapshot_{float(lv):.6g}.npz")
+                self.snapshots[float(lv)] = self.snapshot(path)
         return np.asarray(reac), np.asarray(its)

@@ -39,11 +39,11 @@ def test_binding_declares_every_symbol():
 
 def test_loads_and_reports_version_without_gpu(lib):
     L = _lib.load()
-    assert L.lgdm_abi_version() == 1
+    assert L.lgdm_abi_version() == _lib.ABI_VERSION == 2
     assert L.lgdm_status_string(4) == b"Newton did not converge"
     o = _lib.Options()
     assert L.lgdm_default_options(ctypes.byref(o)) == 0
-    assert o.max_newton == 50 and o.newton_tol == 1e-8
+    assert o.max_newton == 50 and o.newton_tol == 1e-8 and o.wait_limit_s == 2.0
 
 
 def test_workspace_size_host_only(lib):

@@ -170,33 +170,7 @@ def test_bar_curve_fp32_tangent():
 GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
 
 
-# Accuracy of each result against the FP64 oracle (peak load and dissipated
-# energy relative, damage field absolute over all Gauss points): the FP64 path
-# to curve parity, the FP32-tangent path (inexact Newton) to its own targets.
-# Both sides stop Newton at increments of 1e-8 relative, so a converged
-# micro-strain field carries errors of that order, and the damage slope
-# dD/dkappa (up to ~1e4 here) turns them into damage differences of ~1e-8:
-# the FP64 damage bound is 1e-7.
-ACCURACY = {"fp64": {"curve": 1e-6, "peak": 1e-6, "dissipated": 1e-6, "damage": 1e-7},
-            "fp32": {"curve": 1e-6, "peak": 1e-4, "dissipated": 1e-4, "damage": 1e-5}}
-
-
-def _accuracy(p, g, reac, psi, dmg):
-    """Errors of a GPU run against a stored oracle run; dissipated energy is
-    the external work (trapezoid rule over the load-displacement points) minus
-    the stored energy (Eq. 1) at the last committed state."""
-    load = np.concatenate([[0.0], np.asarray(g["load"])])
-    rp = np.concatenate([[0.0], reac])
-    w_ext = float(np.sum(0.5 * (rp[1:] + rp[:-1]) * np.diff(load)))
-    ref = np.asarray(g["reaction"])
-    out = {"curve": np.abs(reac - ref).max() / np.abs(ref).max(),
-           "peak": abs(reac.max() - ref.max()) / abs(ref.max()),
-           "dissipated": abs((w_ext - psi) - g["dissipated"][-1]) / abs(g["dissipated"][-1])}
-    if "damage_final" in g:
-        dref = np.zeros(g["damage_final"]["n_gp"])
-        dref[np.asarray(g["damage_final"]["idx"], dtype=np.int64)] = g["damage_final"]["val"]
-        out["damage"] = np.abs(dmg - dref).max()
-    return out
+from _parity import ACCURACY, accuracy as _accuracy  # noqa: E402
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
@@ -215,6 +189,24 @@ def test_full_size_plate_prefix_against_oracle(precision):
     s.close()
     err = _accuracy(p, g, reac, psi, dmg)
     print(f"\naccuracy {precision} plate 200x200, 30 steps:", {k: f"{v:.2e}" for k, v in err.items()})
+    for k, v in err.items():
+        assert v <= ACCURACY[precision][k], (k, v)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_beam_reduced_accuracy_against_stored_oracle(precision):
+    """Notched beam in three-point bending at 40 x 8 x 8 hexahedra (the 3D
+    workload's geometry and material on a coarser mesh), the oracle's first 90
+    of 300 load steps (peak at step 28, softening to 83 N): curve, peak load,
+    dissipated energy and the final damage field (Eq. 11a-f in 3D)."""
+    g = json.load(open(os.path.join(GOLDEN, "tpb_beam_40x8x8_90.json")))
+    p = li.tpb_beam_problem(40, 8, 8)
+    s = _sim(p, precision=precision)
+    reac, its = s.run(g["load"])
+    psi, dmg = s.energy(), s.field("damage")
+    s.close()
+    err = _accuracy(p, g, reac, psi, dmg)
+    print(f"\naccuracy {precision} beam 40x8x8, 90 steps:", {k: f"{v:.2e}" for k, v in err.items()})
     for k, v in err.items():
         assert v <= ACCURACY[precision][k], (k, v)
 

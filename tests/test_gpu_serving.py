@@ -1,6 +1,9 @@
 """Continuous-batching server: admission by device-memory budget, resident
 state, interleaved load steps, slot reuse; each result bitwise equal to the
 same request run alone."""
+import json
+import os
+
 import numpy as np
 import pytest
 
@@ -54,3 +57,33 @@ def test_admission_respects_budget():
     assert rep["peak_resident_bytes"] <= rep["budget_bytes"]
     with pytest.raises(ValueError):
         Server(budget_bytes=big // 2, precision="fp32").submit(jobs[np.argmax([j.problem.mesh.nel for j in jobs])])
+
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_served_plate_and_beam_against_oracle(precision):
+    """Requests 14 (56 x 56 notched plate, 30 load steps) and 7 (42 x 8 x 8
+    notched beam, 40 load steps) of the seeded trace, served together with two
+    other trace requests by the continuous-batching server, against the
+    oracle's stored runs of the same requests: curve, peak load, dissipated
+    energy (kept by the library) and the final damage field."""
+    from paper_2301_06503_gb300.serve import Job, Server
+    from _parity import ACCURACY, accuracy
+    trace = li.serving_trace()
+    cases = {14: ("trace_plate_r14_30.json", 30), 7: ("trace_beam_r7_40.json", 40)}
+    for k, (f, _) in cases.items():
+        if not os.path.exists(os.path.join(GOLDEN, f)):
+            pytest.skip(f"oracle run {f} not stored")
+    jobs = [Job(k, trace[k].problem, 0.0, n) for k, (_, n) in cases.items()]
+    jobs += [Job(k, trace[k].problem, 0.0, 4) for k in (16, 17)]      # two small plates join the mix
+    srv = Server(budget_bytes=8 << 30, max_resident=3, precision=precision, keep_fields=True)
+    rep = srv.run(jobs)
+    assert rep["completed"] == len(jobs) and rep["failed"] == 0
+    for j in jobs[:2]:
+        g = json.load(open(os.path.join(GOLDEN, cases[j.rid][0])))
+        err = accuracy(j.problem, g, j.reactions, j.psi, j.damage, dissipated=j.dissipated)
+        print(f"\nserved {precision} request {j.rid}:", {k: f"{v:.2e}" for k, v in err.items()})
+        for k, v in err.items():
+            assert v <= ACCURACY[precision][k], (j.rid, k, v)

@@ -52,12 +52,36 @@ def test_replica_totals_single_rank():
 
 # ------------------------------------------------------------------ serving
 class _FakeSim:
-    """Stand-in for a resident simulation: no device work."""
+    """Stand-in for a resident simulation: no device work.  A load step
+    converges at its second Newton iteration; the reaction after step n is n;
+    the stored energy is 0.25; a mesh with ``fails_at = n`` diverges in load
+    step n and its load-step driver then reports non-convergence."""
     live = 0
 
     def __init__(self, mesh, material, bcs, **kw):
         _FakeSim.live += 1
-        self.mesh, self.steps = mesh, 0
+        self.mesh, self.steps, self.iters = mesh, 0, 0
+        self.load, self.load_commit, self.w_ext = 0.0, 0.0, 0.0
+
+    def begin_step(self, load):
+        self.load, self.iters = load, 0
+
+    def _commit(self):
+        r_old = float(self.steps)
+        self.steps += 1
+        self.w_ext += 0.5 * (r_old + self.steps) * (self.load - self.load_commit)
+        self.load_commit = self.load
+
+    def commit(self):
+        self._commit()
+
+    def run_step(self, load):
+        from paper_2301_06503_gb300._lib import LgdmError
+        if getattr(self.mesh, "fails_at", None) == self.steps + 1:
+            raise LgdmError(4, "no convergence")
+        self.begin_step(load)
+        self._commit()
+        return 2
 
     def reaction(self):
         return float(self.steps)
@@ -65,8 +89,11 @@ class _FakeSim:
     def counters(self):
         return {"krylov_iters": 10 * self.steps}
 
-    def energy(self):
-        return 0.25
+    def committed(self):
+        return self.load_commit, self.w_ext, float(self.steps)
+
+    def dissipated_energy(self):
+        return self.w_ext - 0.25, 0.25
 
     def close(self):
         _FakeSim.live -= 1
@@ -85,11 +112,15 @@ class _FakeBatch:
     def set_tuning(self, *a):
         pass
 
-    def run_step(self, loads):
+    def newton_step(self, active=None):
+        conv = []
         for s in self.sims:
-            s.steps += 1
-        fail = [1 if getattr(s.mesh, "fails_at", None) == s.steps else 0 for s in self.sims]
-        return np.full(len(self.sims), 3, np.int32), np.asarray(fail, np.int32) * 4
+            s.iters += 1
+            if getattr(s.mesh, "fails_at", None) == s.steps + 1:
+                conv.append(-1)
+            else:
+                conv.append(1 if s.iters >= 2 else 0)
+        return np.asarray(conv, np.int32), np.full(len(self.sims), 5, np.int32)
 
     def close(self):
         pass
@@ -139,8 +170,12 @@ def test_server_budget_slots_and_reuse(serve):
     assert [r["rid"] for r in rec] == list(range(len(jobs)))
     r0 = rec[0]
     assert r0["load_steps"] == 3 and r0["peak_load"] == 3.0 and r0["krylov_iters"] == 30
+    assert r0["newton_iters"] == 6                   # two batched Newton iterations per load step
     w_ext = 0.001 * (0.5 * (0 + 1) + 0.5 * (1 + 2) + 0.5 * (2 + 3))
+    assert abs(r0["external_work"] - w_ext) <= 1e-15
     assert abs(r0["dissipated_energy"] - (w_ext - 0.25)) <= 1e-15
+    # arrivals join between Newton iterations: two ticks per load step
+    assert srv.ticks >= 2 * max(j.n_steps for j in jobs)
 
 
 def test_server_retires_a_failed_request(serve):
@@ -149,7 +184,8 @@ def test_server_retires_a_failed_request(serve):
     srv = serve.Server(budget_bytes=100, max_resident=4, stream=object(), autotune=False)
     rep = srv.run(jobs)
     assert rep["completed"] == 1 and rep["failed"] == 1
-    assert jobs[0].step == 2 and jobs[1].step == 5
+    assert jobs[0].step == 1 and jobs[1].step == 5     # the failure came in load step 2
+    assert jobs[0].status == 4 and jobs[0].reactions == [1.0]
     assert _FakeSim.live == 0
 
 
