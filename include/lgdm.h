@@ -62,7 +62,16 @@ typedef enum { LGDM_L2 = 1, LGDM_Q4 = 2, LGDM_H8 = 3 } lgdm_elem;
  * test stay double. */
 typedef enum { LGDM_PREC_FP64 = 0, LGDM_PREC_FP32_TANGENT = 1 } lgdm_precision;
 
-typedef enum { LGDM_PRECOND_JACOBI = 0, LGDM_PRECOND_NODE_BLOCK = 1 } lgdm_precond;
+/* Preconditioner of the BiCGSTAB solve.  JACOBI: the diagonal; NODE_BLOCK:
+ * the inverse of each node's nd x nd diagonal block; MULTIGRID: one V-cycle
+ * of aggregation multigrid -- node aggregates of a node and its neighbours
+ * (coarsened to at most 24 nodes, at most 10 levels), piecewise-constant
+ * prolongation, Galerkin coarse matrices (fixed-order sums of the finer
+ * level's node blocks, no atomics), one damped (0.7) node-block Jacobi sweep
+ * before and after each coarse correction, and a dense inverse of the
+ * coarsest matrix.  The multigrid set-up runs after every assembly.  The
+ * GMRES fallback always uses the node blocks. */
+typedef enum { LGDM_PRECOND_JACOBI = 0, LGDM_PRECOND_NODE_BLOCK = 1, LGDM_PRECOND_MULTIGRID = 2 } lgdm_precond;
 
 typedef enum {
   LGDM_FIELD_U = 0,          /* [ndof]  current nodal dofs (interleaved)         */
@@ -133,7 +142,7 @@ typedef struct {
 int32_t lgdm_abi_version(void);
 const char *lgdm_status_string(lgdm_status s);
 
-/* Fill *opt with the defaults (FP64, node-block Jacobi, tol 1e-8, rtol 1e-8,
+/* Fill *opt with the defaults (FP64, multigrid preconditioner, tol 1e-8, rtol 1e-8,
  * 50 Newton iterations, 5000 Krylov iterations, 6 halvings, GMRES(64)
  * fallback, 2 s device wait limit). */
 lgdm_status lgdm_default_options(lgdm_options *opt);

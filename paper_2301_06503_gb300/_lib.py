@@ -11,7 +11,7 @@ LIB_PATH = os.path.join(PKG, "liblgdm.so")
 
 L2, Q4, H8 = 1, 2, 3
 PREC_FP64, PREC_FP32_TANGENT = 0, 1
-PRECOND_JACOBI, PRECOND_NODE_BLOCK = 0, 1
+PRECOND_JACOBI, PRECOND_NODE_BLOCK, PRECOND_MULTIGRID = 0, 1, 2
 FIELD_U, FIELD_KAPPA_HIST, FIELD_DAMAGE, FIELD_DELTA, FIELD_RESIDUAL, FIELD_RHS = range(6)
 NPHASES = 6
 PHASES = ("element", "gather", "precond", "krylov", "commit", "begin_step")

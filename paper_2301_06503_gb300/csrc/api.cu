@@ -110,6 +110,8 @@ lgdm_status build_pattern(const lgdm_mesh &m, Pattern &P, bool with_contrib, std
   return LGDM_OK;
 }
 
+int64_t nd_sq(int nd) { return (int64_t)nd * nd; }
+
 // Bump allocator over the caller's workspace; with base == nullptr it only counts.
 struct Carver {
   char *base;
@@ -189,6 +191,16 @@ struct lgdm_sim {
   int secant = 0, secant_dev = 0;
   bool step_secant = false;
   int secant_streak = 0;
+  // aggregation multigrid: host hierarchy, device level descriptors and
+  // arrays, launch prefixes of the set-up ([level][0..3]: pair blocks {0,
+  // n}, node blocks {0, n})
+  AmgHost amgh;
+  int amg_levels = 0, amg_sb = 0;
+  std::vector<AmgLevel> h_lev;
+  AmgLevel *d_lev = nullptr;
+  double *amg_cinv = nullptr;
+  int64_t *d_amg_prefix = nullptr;
+  std::vector<int64_t> amg_pblocks, amg_nblocks;   // per level: set-up blocks
   // host copies
   std::vector<int32_t> h_nbr_ptr, h_nbr;
   std::string err;
@@ -344,6 +356,50 @@ void carve(lgdm_sim &s, Carver &c) {
   s.d_one = c.take<int32_t>(2);
   s.d_prefix = c.take<int64_t>(6);
   s.d_gstart = c.take<int32_t>(2);
+  const int L = s.amg_levels;
+  s.h_lev.assign(L, AmgLevel{});
+  if (L > 0) {
+    s.d_lev = c.take<AmgLevel>(L);
+    s.d_amg_prefix = c.take<int64_t>((size_t)4 * L);
+    const size_t ts = s.tsize, nd = (size_t)s.nd;
+    for (int l = 0; l < L; ++l) {
+      const AmgHost::Lev &H = s.amgh.lev[l];
+      AmgLevel &V = s.h_lev[l];
+      V.nnode = H.nnode;
+      const size_t n = (size_t)H.nnode;
+      if (l == 0) {
+        V.npairs = (int32_t)s.npairs;
+      } else {
+        V.npairs = H.nbr_ptr.empty() ? 0 : H.nbr_ptr.back();
+        const size_t np = (size_t)V.npairs, nprev = (size_t)s.amgh.lev[l - 1].nnode;
+        const size_t npprev = (l == 1) ? (size_t)s.npairs : (size_t)s.h_lev[l - 1].npairs;
+        V.nbr_ptr = c.take<int32_t>(n + 1);
+        V.nbr = c.take<int32_t>(np);
+        V.pair_node = c.take<int32_t>(np);
+        V.diag_pair = c.take<int32_t>(n);
+        V.mem_ptr = c.take<int32_t>(n + 1);
+        V.mem = c.take<int32_t>(nprev);
+        V.cmap_ptr = c.take<int32_t>(np + 1);
+        V.cmap = c.take<int32_t>(npprev);
+        V.vals = c.take<char>(nd * nd * np * ts);
+        V.minv = c.take<char>(nd * nd * n * ts);
+        V.v = c.take<double>(nd * n);
+        V.z = c.take<double>(nd * n);
+      }
+      if (l + 1 < L) V.agg = c.take<int32_t>(n);
+      V.X = c.take<double>(nd * n);
+      V.R = c.take<double>(nd * n);
+    }
+    const int64_t nc = s.amgh.lev[L - 1].nnode;
+    s.amg_cinv = (nc <= AMG_COARSE_MAX) ? c.take<double>((size_t)(nd_sq(s.nd) * nc * nc)) : nullptr;
+    AmgLevel &V0 = s.h_lev[0];                 // level 0 is the system itself
+    V0.nbr_ptr = s.nbr_ptr;
+    V0.nbr = s.nbr;
+    V0.pair_node = s.pair_node;
+    V0.diag_pair = s.diag_pair;
+    V0.vals = s.vals;
+    V0.minv = s.minv;
+  }
   s.ws_needed = c.off + 256;
 }
 
@@ -393,6 +449,16 @@ lgdm_status plan(lgdm_sim &s, const lgdm_mesh &m, const lgdm_options &o, const l
   if (st != LGDM_OK) return fail(nullptr, st, err);
   s.npairs = pat.npairs;
   s.nnz = pat.npairs * s.nd * s.nd;
+  s.amg_levels = 0;
+  if (o.precond == LGDM_PRECOND_MULTIGRID) {
+    if (!amg_build(s.nnode, pat.nbr_ptr, pat.nbr, s.amgh))
+      return fail(nullptr, LGDM_ERR_INVALID_ARG, "the mesh's node graph does not coarsen for the multigrid");
+    s.amg_levels = (int)s.amgh.lev.size();
+    int sb = s.amg_levels - 1;
+    for (int l = 0; l < s.amg_levels; ++l)
+      if (s.amgh.lev[l].nnode <= AMG_SINGLE_BLOCK) { sb = l; break; }
+    s.amg_sb = sb;
+  }
   s.ncontrib = (int64_t)s.nel * s.nen * s.nen;
   s.ndir = bcs ? bcs->n_dir : 0;
   if (krylov_min_blocks(s.nnode) < 1 || krylov_min_blocks(s.nnode) > (query_device ? max_krylov_blocks(
@@ -413,6 +479,32 @@ namespace {
 
 KrylovArgs krylov_args(lgdm_sim *s);
 
+// Multigrid set-up of a simulation after its assembly and fine block-Jacobi
+// inverses: Galerkin values and inverses level by level, then the dense
+// inverse of the coarsest level.
+template <typename TT>
+cudaError_t multigrid_setup(lgdm_sim *s) {
+  const int32_t *mem = s->d_one, *act = s->d_one + 1;
+  for (int l = 1; l < s->amg_levels; ++l) {
+    const cudaError_t e = launch_batch_amg_level<TT>(s->nd, l, s->d_self, mem, s->d_amg_prefix + 4 * l,
+                                                     s->d_amg_prefix + 4 * l + 2, 1, s->amg_pblocks[l],
+                                                     s->amg_nblocks[l], act, s->stream);
+    if (e != cudaSuccess) return e;
+  }
+  if (s->amg_levels > 0 && s->amg_cinv) return launch_batch_amg_coarse<TT>(s->nd, s->d_self, mem, 1, act, s->stream);
+  return cudaSuccess;
+}
+
+AmgInfo amg_info(const lgdm_sim *s) {
+  AmgInfo m{};
+  m.lev = s->d_lev;
+  m.nlev = s->amg_levels;
+  m.sb_level = s->amg_sb;
+  m.cinv = s->amg_cinv;
+  m.nc = s->amg_levels > 0 ? s->h_lev[s->amg_levels - 1].nnode : 0;
+  return m;
+}
+
 BatchSim self_desc(lgdm_sim *s) {
   BatchSim d{};
   d.m = s->mesh_view();
@@ -426,7 +518,8 @@ BatchSim self_desc(lgdm_sim *s) {
   d.rraw = s->rraw;
   d.rhs = s->rhs;
   d.minv = s->minv;
-  d.precond = s->opt.precond;
+  d.precond = (s->opt.precond == LGDM_PRECOND_JACOBI) ? LGDM_PRECOND_JACOBI : LGDM_PRECOND_NODE_BLOCK;
+  d.amg = amg_info(s);
   return d;
 }
 
@@ -454,7 +547,7 @@ const char *lgdm_status_string(lgdm_status s) {
 lgdm_status lgdm_default_options(lgdm_options *o) {
   if (!o) return fail(nullptr, LGDM_ERR_INVALID_ARG, "options is NULL");
   o->precision = LGDM_PREC_FP64;
-  o->precond = LGDM_PRECOND_NODE_BLOCK;
+  o->precond = LGDM_PRECOND_MULTIGRID;
   o->newton_tol = 1e-8;
   o->krylov_rtol = 1e-8;
   o->max_newton = 50;
@@ -525,6 +618,8 @@ lgdm_status lgdm_create(const lgdm_mesh *m, const lgdm_material *mat, const lgdm
       return fail(nullptr, LGDM_ERR_INVALID_ARG, "workspace NULL or not 256-byte aligned");
     if (o->precision != LGDM_PREC_FP64 && o->precision != LGDM_PREC_FP32_TANGENT)
       return fail(nullptr, LGDM_ERR_INVALID_ARG, "unknown precision");
+    if (o->precond < LGDM_PRECOND_JACOBI || o->precond > LGDM_PRECOND_MULTIGRID)
+      return fail(nullptr, LGDM_ERR_INVALID_ARG, "unknown preconditioner");
     if (o->max_newton < 1 || o->max_krylov < 1 || o->max_halvings < 0 || !(o->newton_tol > 0.0))
       return fail(nullptr, LGDM_ERR_INVALID_ARG, "bad iteration limits or tolerance");
     if (o->gmres_m < 0 || o->gmres_m > GMRES_MAX_M)
@@ -614,6 +709,38 @@ lgdm_status lgdm_create(const lgdm_mesh *m, const lgdm_material *mat, const lgdm
     e = e ? e : cudaMemsetAsync(s->u_commit, 0, sizeof(double) * s->ndof, st_);
     e = e ? e : cudaMemsetAsync(s->reaction, 0, 3 * sizeof(double), st_);
     e = e ? e : cudaMemsetAsync(s->res, 0, sizeof(SolveResult), st_);
+    // multigrid levels: pattern, maps, descriptors and set-up prefixes
+    std::vector<int64_t> amg_prefix;
+    if (s->amg_levels > 0) {
+      const int L = s->amg_levels;
+      s->amg_pblocks.assign(L, 0);
+      s->amg_nblocks.assign(L, 0);
+      amg_prefix.assign((size_t)4 * L, 0);
+      for (int l = 0; l < L; ++l) {
+        const AmgHost::Lev &H = s->amgh.lev[l];
+        AmgLevel &V = s->h_lev[l];
+        auto upv = [&](const int32_t *dst, const std::vector<int32_t> &v) {
+          if (e == cudaSuccess && !v.empty()) e = up(const_cast<int32_t *>(dst), v.data(), sizeof(int32_t) * v.size());
+        };
+        if (l > 0) {
+          upv(V.nbr_ptr, H.nbr_ptr);
+          upv(V.nbr, H.nbr);
+          upv(V.pair_node, H.pair_node);
+          upv(V.diag_pair, H.diag_pair);
+          upv(V.mem_ptr, H.mem_ptr);
+          upv(V.mem, H.mem);
+          upv(V.cmap_ptr, H.cmap_ptr);
+          upv(V.cmap, H.cmap);
+          s->amg_pblocks[l] = (V.npairs + 255) / 256;
+          s->amg_nblocks[l] = (V.nnode + 127) / 128;
+          amg_prefix[4 * l + 1] = s->amg_pblocks[l];
+          amg_prefix[4 * l + 3] = s->amg_nblocks[l];
+        }
+        if (l + 1 < L) upv(V.agg, H.agg);
+      }
+      e = e ? e : up(s->d_lev, s->h_lev.data(), sizeof(AmgLevel) * L);
+      e = e ? e : up(s->d_amg_prefix, amg_prefix.data(), sizeof(int64_t) * amg_prefix.size());
+    }
     BatchSim self{};
     KrylovArgs kself{};
     int32_t one[2] = {0, 1};
@@ -636,6 +763,7 @@ lgdm_status lgdm_create(const lgdm_mesh *m, const lgdm_material *mat, const lgdm
       e = e ? e : up(s->d_gstart, gstart, sizeof(gstart));
     }
     e = e ? e : cudaStreamSynchronize(st_);   // host staging vectors die at return
+    s->amgh = AmgHost();                      // the device holds the hierarchy now
     if (e != cudaSuccess) {
       const std::string msg = std::string("upload failed: ") + cudaGetErrorString(e);
       delete s;
@@ -781,6 +909,7 @@ lgdm_status lgdm_assemble(lgdm_sim *s) {
     {
       PhaseTimer pt(s, 2);
       LGDM_CUDA(s, launch_batch_precond<float>(s->nd, s->d_self, mem, pb, 1, s->self_pblocks, act, s->stream));
+      LGDM_CUDA(s, multigrid_setup<float>(s));
     }
   } else {
     {
@@ -794,9 +923,10 @@ lgdm_status lgdm_assemble(lgdm_sim *s) {
     {
       PhaseTimer pt(s, 2);
       LGDM_CUDA(s, launch_batch_precond<double>(s->nd, s->d_self, mem, pb, 1, s->self_pblocks, act, s->stream));
+      LGDM_CUDA(s, multigrid_setup<double>(s));
     }
   }
-  s->counters[0] += 3;
+  s->counters[0] += 3 + (s->amg_levels > 0 ? 2 * (s->amg_levels - 1) + (s->amg_cinv ? 1 : 0) : 0);
   s->counters[1] += 1;
   s->assembled = true;
   return LGDM_OK;
@@ -873,6 +1003,7 @@ KrylovArgs krylov_args(lgdm_sim *s) {
   a.res = s->res;
   a.wait_ns = (unsigned long long)(s->opt.wait_limit_s * 1e9);
   a.barrier_extra = 0;
+  a.amg = amg_info(s);
   return a;
 }
 
@@ -1269,12 +1400,22 @@ struct lgdm_batch {
   KrylovArgs *d_kargs = nullptr;
   int32_t *d_active = nullptr;
   SolveResult *d_res = nullptr;
+  struct AmgLaunch {                   // multigrid set-up of one level for the members that have it
+    int level = 0;
+    int nm = 0;
+    int32_t *d_members = nullptr;
+    int64_t *d_pb = nullptr, *d_nb = nullptr;
+    int64_t tot_pb = 0, tot_nb = 0;
+  };
   struct Group {                       // members of one element type
     int elem = 0, nd = 0;
     std::vector<int32_t> members;
     int32_t *d_members = nullptr;
     int64_t *d_tile = nullptr, *d_gblock = nullptr, *d_pblock = nullptr;
     int64_t tiles = 0, gblocks = 0, pblocks = 0;
+    std::vector<AmgLaunch> amg;
+    int n_coarse = 0;
+    int32_t *d_coarse = nullptr;       // members with a dense coarsest inverse
   };
   std::vector<Group> groups;
   struct Wave {                        // members whose block groups fit one co-resident launch
@@ -1294,6 +1435,9 @@ struct lgdm_batch {
   std::vector<int32_t> h_secant;       // tangent mode written into each member's descriptor
   std::vector<SolveResult> h_res;
   std::string err;
+  // host sources of asynchronous uploads at creation (kept until the stream has synchronised)
+  std::vector<std::vector<int32_t>> amg_staging;
+  std::vector<std::vector<int64_t>> amg_staging64;
   // phase timers: events before the element launches, after them, after the
   // gathers, after the preconditioner set-ups and after the first solve
   bool timers_on = false;
@@ -1311,8 +1455,10 @@ namespace {
 
 size_t batch_bytes(int n) {
   // descriptors, flags, results and prefix arrays; a generous bound per member
+  const size_t amg = (size_t)3 * AMG_MAX_LEVELS * ((size_t)n * 4 + 2 * (size_t)(n + 1) * 8 + 3 * 256) +
+                     (size_t)3 * ((size_t)n * 4 + 256);
   return (size_t)n * (sizeof(BatchSim) + sizeof(KrylovArgs) + sizeof(SolveResult) + 4 * 64 + 10 * 8) +
-         (size_t)(n + 8) * 8 * 24 + (1 << 16);
+         (size_t)(n + 8) * 8 * 24 + amg + (1 << 16);
 }
 
 lgdm_status bfail(lgdm_batch *b, lgdm_status st, const std::string &m) {
@@ -1364,6 +1510,18 @@ lgdm_status batch_issue_assembly(lgdm_batch *b) {
     else
       LGDM_BCUDA(b, launch_batch_precond<double>(g.nd, b->d_sims, g.d_members, g.d_pblock, (int)g.members.size(),
                                                  g.pblocks, b->d_active, b->stream));
+    for (const auto &al : g.amg) {
+      if (b->fp32)
+        LGDM_BCUDA(b, launch_batch_amg_level<float>(g.nd, al.level, b->d_sims, al.d_members, al.d_pb, al.d_nb, al.nm,
+                                                    al.tot_pb, al.tot_nb, b->d_active, b->stream));
+      else
+        LGDM_BCUDA(b, launch_batch_amg_level<double>(g.nd, al.level, b->d_sims, al.d_members, al.d_pb, al.d_nb, al.nm,
+                                                     al.tot_pb, al.tot_nb, b->d_active, b->stream));
+    }
+    if (b->fp32)
+      LGDM_BCUDA(b, launch_batch_amg_coarse<float>(g.nd, b->d_sims, g.d_coarse, g.n_coarse, b->d_active, b->stream));
+    else
+      LGDM_BCUDA(b, launch_batch_amg_coarse<double>(g.nd, b->d_sims, g.d_coarse, g.n_coarse, b->d_active, b->stream));
   }
   LGDM_BMARK(b, 3);
   return LGDM_OK;
@@ -1495,7 +1653,8 @@ lgdm_status lgdm_batch_create(lgdm_sim *const *sims, int32_t n, void *ws, size_t
       d.rraw = s->rraw;
       d.rhs = s->rhs;
       d.minv = s->minv;
-      d.precond = s->opt.precond;
+      d.precond = (s->opt.precond == LGDM_PRECOND_JACOBI) ? LGDM_PRECOND_JACOBI : LGDM_PRECOND_NODE_BLOCK;
+      d.amg = amg_info(s);
       hk[i] = krylov_args(s);
     }
     // element-type groups
@@ -1524,6 +1683,44 @@ lgdm_status lgdm_batch_create(lgdm_sim *const *sims, int32_t n, void *ws, size_t
       }
       g.gblocks = gb[m];
       g.pblocks = pbk[m];
+      // multigrid set-up launches: per level, the members that have it
+      int maxl = 0;
+      for (int j = 0; j < m; ++j) maxl = std::max(maxl, b->sims[g.members[j]]->amg_levels);
+      for (int l = 1; l < maxl; ++l) {
+        lgdm_batch::AmgLaunch al;
+        al.level = l;
+        std::vector<int32_t> mm;
+        std::vector<int64_t> pbv(1, 0), nbv(1, 0);
+        for (int j = 0; j < m; ++j) {
+          lgdm_sim *s = b->sims[g.members[j]];
+          if (s->amg_levels <= l) continue;
+          mm.push_back(g.members[j]);
+          pbv.push_back(pbv.back() + s->amg_pblocks[l]);
+          nbv.push_back(nbv.back() + s->amg_nblocks[l]);
+        }
+        al.nm = (int)mm.size();
+        al.tot_pb = pbv.back();
+        al.tot_nb = nbv.back();
+        al.d_members = c.take<int32_t>(al.nm);
+        al.d_pb = c.take<int64_t>(al.nm + 1);
+        al.d_nb = c.take<int64_t>(al.nm + 1);
+        LGDM_BCUDA(b, cudaMemcpyAsync(al.d_members, mm.data(), sizeof(int32_t) * al.nm, cudaMemcpyHostToDevice, b->stream));
+        LGDM_BCUDA(b, cudaMemcpyAsync(al.d_pb, pbv.data(), sizeof(int64_t) * (al.nm + 1), cudaMemcpyHostToDevice, b->stream));
+        LGDM_BCUDA(b, cudaMemcpyAsync(al.d_nb, nbv.data(), sizeof(int64_t) * (al.nm + 1), cudaMemcpyHostToDevice, b->stream));
+        g.amg.push_back(std::move(al));
+        b->amg_staging.push_back(std::move(mm));
+        b->amg_staging64.push_back(std::move(pbv));
+        b->amg_staging64.push_back(std::move(nbv));
+      }
+      std::vector<int32_t> cm;
+      for (int j = 0; j < m; ++j)
+        if (b->sims[g.members[j]]->amg_cinv) cm.push_back(g.members[j]);
+      g.n_coarse = (int)cm.size();
+      g.d_coarse = c.take<int32_t>(std::max(g.n_coarse, 1));
+      if (g.n_coarse > 0)
+        LGDM_BCUDA(b, cudaMemcpyAsync(g.d_coarse, cm.data(), sizeof(int32_t) * g.n_coarse, cudaMemcpyHostToDevice,
+                                      b->stream));
+      b->amg_staging.push_back(std::move(cm));
       LGDM_BCUDA(b, cudaMemcpyAsync(g.d_members, g.members.data(), sizeof(int32_t) * m, cudaMemcpyHostToDevice, b->stream));
       LGDM_BCUDA(b, cudaMemcpyAsync(g.d_gblock, gb.data(), sizeof(int64_t) * (m + 1), cudaMemcpyHostToDevice, b->stream));
       LGDM_BCUDA(b, cudaMemcpyAsync(g.d_pblock, pbk.data(), sizeof(int64_t) * (m + 1), cudaMemcpyHostToDevice, b->stream));
@@ -1600,6 +1797,8 @@ lgdm_status lgdm_batch_create(lgdm_sim *const *sims, int32_t n, void *ws, size_t
       LGDM_BCUDA(b, cudaMemcpyAsync(g.d_tile, tl.data(), sizeof(int64_t) * (m + 1), cudaMemcpyHostToDevice, b->stream));
     }
     LGDM_BCUDA(b, cudaStreamSynchronize(b->stream));
+    b->amg_staging.clear();
+    b->amg_staging64.clear();
     *out = b;
     return LGDM_OK;
   } catch (...) {

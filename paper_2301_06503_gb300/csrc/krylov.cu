@@ -197,6 +197,208 @@ __device__ __forceinline__ void reduce_tiles(int64_t n0, int64_t n1, int64_t t0,
   }
 }
 
+// ---------------------------------------------------------------- multigrid V-cycle
+// Loads of the V-cycle vectors.  Grid-wide levels read values other blocks
+// wrote during the launch: through L2 (CG).  The single-block levels read
+// only what their own block wrote since the last __syncthreads: through L1.
+template <bool CG>
+__device__ __forceinline__ double vld(const double *p) {
+  if constexpr (CG) return __ldcg(p);
+  else return *p;
+}
+
+// y = (A_l x~) for node a of level l, with x~[b] = x[b] + zc[agg[b]] when zc
+// is given (the prolonged coarse correction added on the fly).
+template <int ND, typename TT, bool CG>
+__device__ __forceinline__ void lev_spmv(const AmgLevel &L, int64_t a, const double *x, const double *zc,
+                                         double *y) {
+  const int32_t pb = L.nbr_ptr[a], deg = L.nbr_ptr[a + 1] - pb;
+  const TT *v = static_cast<const TT *>(L.vals) + (int64_t)ND * ND * pb;
+  const int64_t rs = (int64_t)ND * deg;
+#pragma unroll
+  for (int i = 0; i < ND; ++i) y[i] = 0.0;
+#pragma unroll 3
+  for (int32_t s = 0; s < deg; ++s) {
+    const int32_t b = L.nbr[pb + s];
+    double xv[ND];
+#pragma unroll
+    for (int j = 0; j < ND; ++j) xv[j] = vld<CG>(x + (int64_t)ND * b + j);
+    if (zc) {
+      const double *zb = zc + (int64_t)ND * L.agg[b];
+#pragma unroll
+      for (int j = 0; j < ND; ++j) xv[j] += vld<CG>(zb + j);
+    }
+#pragma unroll
+    for (int i = 0; i < ND; ++i)
+#pragma unroll
+      for (int j = 0; j < ND; ++j) y[i] += (double)v[i * rs + ND * s + j] * xv[j];
+  }
+}
+
+// X[a] = omega M_l^-1 v[a]  (v read through L2: it may come from another block)
+template <int ND, typename TT>
+__device__ __forceinline__ void lev_presmooth(const AmgLevel &L, int64_t a, const double *v, double *X) {
+  double in[ND], out[ND];
+#pragma unroll
+  for (int i = 0; i < ND; ++i) in[i] = __ldcg(v + ND * a + i);
+  precond_apply<ND, TT>(static_cast<const TT *>(L.minv), a, in, out);
+#pragma unroll
+  for (int i = 0; i < ND; ++i) X[ND * a + i] = AMG_OMEGA * out[i];
+}
+
+// R[a] = v[a] - (A_l X)[a]
+template <int ND, typename TT, bool CG>
+__device__ __forceinline__ void lev_residual(const AmgLevel &L, int64_t a, const double *v, const double *X,
+                                             double *R) {
+  double y[ND];
+  lev_spmv<ND, TT, CG>(L, a, X, nullptr, y);
+#pragma unroll
+  for (int i = 0; i < ND; ++i) R[ND * a + i] = __ldcg(v + ND * a + i) - y[i];
+}
+
+// v_c[I] = sum of R over the members of aggregate I (fixed order); with
+// Xc given also Xc[I] = omega M_c^-1 v_c[I].
+template <int ND, typename TT, bool CG>
+__device__ __forceinline__ void lev_restrict(const AmgLevel &C, int64_t I, const double *R, double *vc, double *Xc) {
+  double acc[ND];
+#pragma unroll
+  for (int i = 0; i < ND; ++i) acc[i] = 0.0;
+  const int32_t m1 = C.mem_ptr[I + 1];
+  for (int32_t m = C.mem_ptr[I]; m < m1; ++m) {
+    const double *r = R + (int64_t)ND * C.mem[m];
+#pragma unroll
+    for (int i = 0; i < ND; ++i) acc[i] += vld<CG>(r + i);
+  }
+#pragma unroll
+  for (int i = 0; i < ND; ++i) vc[ND * I + i] = acc[i];
+  if (Xc) {
+    double out[ND];
+    precond_apply<ND, TT>(static_cast<const TT *>(C.minv), I, acc, out);
+#pragma unroll
+    for (int i = 0; i < ND; ++i) Xc[ND * I + i] = AMG_OMEGA * out[i];
+  }
+}
+
+// Coarse correction and post-smoothing of node a: with x~ = X + P zc,
+// z[a] = x~[a] + omega M_l^-1 (v[a] - (A_l x~)[a]).
+template <int ND, typename TT, bool CG>
+__device__ __forceinline__ void lev_postsmooth(const AmgLevel &L, int64_t a, const double *v, const double *X,
+                                               const double *zc, double *z) {
+  double y[ND], r[ND], out[ND];
+  lev_spmv<ND, TT, CG>(L, a, X, zc, y);
+  const double *za = zc + (int64_t)ND * L.agg[a];
+#pragma unroll
+  for (int i = 0; i < ND; ++i) r[i] = __ldcg(v + ND * a + i) - y[i];
+  precond_apply<ND, TT>(static_cast<const TT *>(L.minv), a, r, out);
+#pragma unroll
+  for (int i = 0; i < ND; ++i) z[ND * a + i] = vld<CG>(X + ND * a + i) + vld<CG>(za + i) + AMG_OMEGA * out[i];
+}
+
+// The V-cycle below level k run by one block: vk in, zk out (levels k ..
+// nlev-1, __syncthreads between the steps).  The coarsest level is solved with
+// its dense inverse, or, without one, by four damped block-Jacobi sweeps.
+template <int ND, typename TT>
+__device__ void amg_single_block(const AmgInfo &M, int k, const double *vk, double *zk) {
+  const AmgLevel *lev = M.lev;
+  const int L = M.nlev;
+  if (k < L - 1)
+    for (int64_t a = threadIdx.x; a < lev[k].nnode; a += KT) lev_presmooth<ND, TT>(lev[k], a, vk, lev[k].X);
+  __syncthreads();
+  for (int l = k; l < L - 1; ++l) {
+    const AmgLevel &F = lev[l], &C = lev[l + 1];
+    const double *v = (l == k) ? vk : F.v;
+    for (int64_t a = threadIdx.x; a < F.nnode; a += KT) lev_residual<ND, TT, false>(F, a, v, F.X, F.R);
+    __syncthreads();
+    for (int64_t I = threadIdx.x; I < C.nnode; I += KT)
+      lev_restrict<ND, TT, false>(C, I, F.R, C.v, (l + 1 < L - 1) ? C.X : nullptr);
+    __syncthreads();
+  }
+  {
+    const AmgLevel &C = lev[L - 1];
+    const double *v = (L - 1 == k) ? vk : C.v;
+    double *z = (L - 1 == k) ? zk : C.z;
+    const int64_t N = (int64_t)ND * C.nnode;
+    if (M.cinv) {
+      for (int64_t i = threadIdx.x; i < N; i += KT) {
+        double acc = 0.0;
+        const double *row = M.cinv + i * N;
+        for (int64_t j = 0; j < N; ++j) acc += row[j] * __ldcg(v + j);
+        z[i] = acc;
+      }
+      __syncthreads();
+    } else {
+      for (int64_t a = threadIdx.x; a < C.nnode; a += KT) lev_presmooth<ND, TT>(C, a, v, C.X);
+      __syncthreads();
+      for (int sweep = 0; sweep < 4; ++sweep) {
+        for (int64_t a = threadIdx.x; a < C.nnode; a += KT) {
+          double y[ND], r[ND], out[ND];
+          lev_spmv<ND, TT, false>(C, a, C.X, nullptr, y);
+#pragma unroll
+          for (int i = 0; i < ND; ++i) r[i] = __ldcg(v + ND * a + i) - y[i];
+          precond_apply<ND, TT>(static_cast<const TT *>(C.minv), a, r, out);
+#pragma unroll
+          for (int i = 0; i < ND; ++i) z[ND * a + i] = C.X[ND * a + i] + AMG_OMEGA * out[i];
+        }
+        __syncthreads();
+        for (int64_t i = threadIdx.x; i < N; i += KT) C.X[i] = z[i];
+        __syncthreads();
+      }
+    }
+  }
+  for (int l = L - 2; l >= k; --l) {
+    const AmgLevel &F = lev[l];
+    const double *v = (l == k) ? vk : F.v;
+    double *z = (l == k) ? zk : F.z;
+    for (int64_t a = threadIdx.x; a < F.nnode; a += KT) lev_postsmooth<ND, TT, false>(F, a, v, F.X, lev[l + 1].z, z);
+    __syncthreads();
+  }
+}
+
+// z = M^-1 vin with M one multigrid V-cycle (one pre- and one post-smoothing
+// sweep of damped block Jacobi per level), for the system of a group of nb
+// blocks.  Level-0 nodes [n0, n1) are this block's; coarse levels above the
+// single-block size are split evenly over the group; the levels from
+// sb_level down are run by the group's first block.  Every value is a per-node
+// fixed-order sum, so z does not depend on the group size.  Returns false if a
+// grid barrier timed out.  On return z is complete for this block's level-0
+// nodes only: the caller's next grid barrier publishes it.
+template <int ND, typename TT>
+__device__ bool amg_apply(const KrylovArgs &A, const double *vin, double *zout, int nb, int bid, unsigned int nbar,
+                          int64_t n0, int64_t n1) {
+  const AmgInfo &M = A.amg;
+  const AmgLevel *lev = M.lev;
+  const int S = M.sb_level;
+  if (S == 0) {
+    if (!grid_barrier(A.bar_count, A.bar_gen, nbar, A.wait_ns)) return false;
+    if (bid == 0) amg_single_block<ND, TT>(M, 0, vin, zout);
+    return true;
+  }
+  for (int64_t a = n0 + threadIdx.x; a < n1; a += KT) lev_presmooth<ND, TT>(lev[0], a, vin, lev[0].X);
+  for (int l = 0; l < S; ++l) {
+    const AmgLevel &F = lev[l], &C = lev[l + 1];
+    const double *v = (l == 0) ? vin : F.v;
+    const int64_t a0 = (l == 0) ? n0 : (int64_t)bid * F.nnode / nb, a1 = (l == 0) ? n1 : (int64_t)(bid + 1) * F.nnode / nb;
+    if (!grid_barrier(A.bar_count, A.bar_gen, nbar, A.wait_ns)) return false;     // X_l published
+    for (int64_t a = a0 + threadIdx.x; a < a1; a += KT) lev_residual<ND, TT, true>(F, a, v, F.X, F.R);
+    if (!grid_barrier(A.bar_count, A.bar_gen, nbar, A.wait_ns)) return false;     // R_l published
+    const int64_t c0 = (int64_t)bid * C.nnode / nb, c1 = (int64_t)(bid + 1) * C.nnode / nb;
+    for (int64_t I = c0 + threadIdx.x; I < c1; I += KT)
+      lev_restrict<ND, TT, true>(C, I, F.R, C.v, (l + 1 < S) ? C.X : nullptr);
+  }
+  if (!grid_barrier(A.bar_count, A.bar_gen, nbar, A.wait_ns)) return false;       // v_S published
+  if (bid == 0) amg_single_block<ND, TT>(M, S, lev[S].v, lev[S].z);
+  if (!grid_barrier(A.bar_count, A.bar_gen, nbar, A.wait_ns)) return false;       // z_S published
+  for (int l = S - 1; l >= 0; --l) {
+    const AmgLevel &F = lev[l];
+    const double *v = (l == 0) ? vin : F.v;
+    double *z = (l == 0) ? zout : F.z;
+    const int64_t a0 = (l == 0) ? n0 : (int64_t)bid * F.nnode / nb, a1 = (l == 0) ? n1 : (int64_t)(bid + 1) * F.nnode / nb;
+    for (int64_t a = a0 + threadIdx.x; a < a1; a += KT) lev_postsmooth<ND, TT, true>(F, a, v, F.X, lev[l + 1].z, z);
+    if (l > 0 && !grid_barrier(A.bar_count, A.bar_gen, nbar, A.wait_ns)) return false;   // z_l published
+  }
+  return true;
+}
+
 // The solver for one system on a group of nb blocks (bid = rank in the group).
 // A thread owns whole nodes: their nd rows in every vector, the node-block
 // preconditioner and the SpMV rows.
@@ -210,6 +412,7 @@ __device__ __forceinline__ void bicgstab_body(const KrylovArgs &A, const int nb,
   const int64_t n0 = min(t0 * T, (int64_t)A.nnode), n1 = min(t1 * T, (int64_t)A.nnode);
   const TT *vals = static_cast<const TT *>(A.vals);
   const TT *minv = static_cast<const TT *>(A.minv);
+  const bool mg = A.amg.nlev > 0;             // preconditioner: multigrid V-cycle, else block Jacobi
   double *P = A.partial;                      // [3 slots][4 values][ntiles]
   auto part = [&](int slot, int k) { return P + ((int64_t)slot * 4 + k) * NT; };
 #define LGDM_NODES for (int64_t a = n0 + threadIdx.x; a < n1; a += KT)
@@ -294,10 +497,13 @@ __device__ __forceinline__ void bicgstab_body(const KrylovArgs &A, const int nb,
           pv[i] = A.r[row] + beta * (A.pv[row] - omega * A.v[row]);
           A.pv[row] = pv[i];
         }
-        precond_apply<ND, TT>(minv, a, pv, ph);
+        if (!mg) {
+          precond_apply<ND, TT>(minv, a, pv, ph);
 #pragma unroll
-        for (int i = 0; i < ND; ++i) A.ph[ND * a + i] = ph[i];
+          for (int i = 0; i < ND; ++i) A.ph[ND * a + i] = ph[i];
+        }
       }
+      if (mg && !(ok = amg_apply<ND, TT>(A, A.pv, A.ph, nb, bid, nbar, n0, n1))) break;
       if (!(ok = grid_barrier(A.bar_count, A.bar_gen, nbar, A.wait_ns))) break;
       LGDM_REDUCE(1, 0, 0) {
         double y[ND];
@@ -327,10 +533,13 @@ __device__ __forceinline__ void bicgstab_body(const KrylovArgs &A, const int nb,
           sv[i] = A.r[row] - alpha * A.v[row];
           A.sv[row] = sv[i];
         }
-        precond_apply<ND, TT>(minv, a, sv, sh);
+        if (!mg) {
+          precond_apply<ND, TT>(minv, a, sv, sh);
 #pragma unroll
-        for (int i = 0; i < ND; ++i) A.sh[ND * a + i] = sh[i];
+          for (int i = 0; i < ND; ++i) A.sh[ND * a + i] = sh[i];
+        }
       }
+      if (mg && !(ok = amg_apply<ND, TT>(A, A.sv, A.sh, nb, bid, nbar, n0, n1))) break;
       if (!(ok = grid_barrier(A.bar_count, A.bar_gen, nbar, A.wait_ns))) break;
       LGDM_REDUCE(2, 1, 0) {
         double y[ND];

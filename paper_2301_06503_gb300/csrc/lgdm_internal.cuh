@@ -3,6 +3,7 @@
 #include <cstdint>
 #include <cstddef>
 #include <string>
+#include <vector>
 #include <cuda_runtime.h>
 #include "lgdm.h"
 
@@ -124,6 +125,49 @@ cudaError_t launch_external_work(double *c, double dload, cudaStream_t s);
 cudaError_t launch_damaged_volume(int elem, const MeshView &m, const MatConst &mc, const double *kh,
                                   double threshold, double *vol, double *part, double *out, cudaStream_t s);
 
+// ---------------------------------------------------------------- aggregation multigrid
+// Levels of the aggregation multigrid preconditioner.  Level 0 is the
+// system's own node-block CSR; level l+1 has one node per aggregate of level
+// l (a node and its neighbours, chosen greedily), the prolongation copies an
+// aggregate's nd values to each of its nodes, the restriction sums them, and
+// the level-(l+1) matrix is the Galerkin product R A_l P: every block of it is
+// the fixed-order sum of the level-l blocks of the node pairs that map to it.
+constexpr int AMG_MAX_LEVELS = 10;
+constexpr int AMG_COARSE_MAX = 24;        // nodes of the coarsest level (dense inverse)
+constexpr int AMG_SINGLE_BLOCK = 2048;    // levels with at most this many nodes run in one block
+constexpr double AMG_OMEGA = 0.7;         // damping of the block-Jacobi smoother
+
+struct AmgLevel {
+  int32_t nnode;
+  int32_t npairs;
+  const int32_t *nbr_ptr, *nbr, *pair_node, *diag_pair;   // pattern (level 0: the system's)
+  void *vals, *minv;                       // TT node-block values and block-Jacobi inverses
+  const int32_t *mem_ptr, *mem;            // members of each node (level >= 1): [nnode+1], [n_{l-1}]
+  const int32_t *cmap_ptr, *cmap;          // Galerkin map (level >= 1): [npairs+1], [npairs_{l-1}]
+  const int32_t *agg;                      // node -> node of the next level (all but the coarsest)
+  double *v, *X, *R, *z;                   // [nd*nnode] V-cycle vectors (level 0: X, R only)
+};
+
+struct AmgInfo {
+  const AmgLevel *lev;                     // [nlev] device array
+  int32_t nlev;                            // 0: no multigrid (block Jacobi)
+  int32_t sb_level;                        // first level run by a single block
+  double *cinv;                            // [(nd n_c)^2] inverse of the coarsest matrix
+  int32_t nc;                              // nodes of the coarsest level
+};
+
+// Host-built hierarchy (pattern only; values are set up per assembly).
+struct AmgHost {
+  struct Lev {
+    int32_t nnode = 0;
+    std::vector<int32_t> nbr_ptr, nbr, pair_node, diag_pair, mem_ptr, mem, cmap_ptr, cmap, agg;
+  };
+  std::vector<Lev> lev;                    // lev[0] holds only agg (the pattern is the system's)
+};
+// Builds the coarse levels from the fine node graph (nbr_ptr, nbr); false if
+// the graph does not coarsen.
+bool amg_build(int32_t nnode, const std::vector<int32_t> &nbr_ptr, const std::vector<int32_t> &nbr, AmgHost &h);
+
 // One member of a batch, as the batched kernels see it.
 struct BatchSim {
   MeshView m;
@@ -136,6 +180,7 @@ struct BatchSim {
   double *rraw, *rhs;
   void *minv;
   int32_t precond;
+  AmgInfo amg;
 };
 int batch_tile_elements(int elem, int bt);
 template <typename TT>
@@ -148,6 +193,17 @@ cudaError_t launch_batch_gather(int elem, const BatchSim *sims, const int32_t *m
 template <typename TT>
 cudaError_t launch_batch_precond(int nd, const BatchSim *sims, const int32_t *members, const int64_t *block_start,
                                  int nm, int64_t total_blocks, const int32_t *active, cudaStream_t s);
+// Multigrid set-up of level l (>= 1) for the members listed: Galerkin values
+// (256 coarse pairs per block, prefix pair_blocks) then block-Jacobi inverses
+// (128 nodes per block, prefix node_blocks).
+template <typename TT>
+cudaError_t launch_batch_amg_level(int nd, int level, const BatchSim *sims, const int32_t *members,
+                                   const int64_t *pair_blocks, const int64_t *node_blocks, int nm, int64_t total_pb,
+                                   int64_t total_nb, const int32_t *active, cudaStream_t s);
+// Dense inverse of each listed member's coarsest level, one block per member.
+template <typename TT>
+cudaError_t launch_batch_amg_coarse(int nd, const BatchSim *sims, const int32_t *members, int nm,
+                                    const int32_t *active, cudaStream_t s);
 
 constexpr int KRYLOV_THREADS = 256;
 
@@ -194,6 +250,7 @@ struct KrylovArgs {
   SolveResult *res;
   unsigned long long wait_ns;  // limit of each grid-barrier wait
   int32_t barrier_extra;       // blocks the barrier waits for beyond those launched (failure injection; 0)
+  AmgInfo amg;                 // nlev > 0: the preconditioner is one multigrid V-cycle
 };
 // mode 0: solve; 1: solve, u += delta, Newton test; 2: update and test only.
 template <typename TT>

@@ -14,7 +14,7 @@ import torch
 from . import _lib as L
 
 _PREC = {"fp64": L.PREC_FP64, "fp32": L.PREC_FP32_TANGENT, "fp32_tangent": L.PREC_FP32_TANGENT}
-_PRECOND = {"jacobi": L.PRECOND_JACOBI, "block": L.PRECOND_NODE_BLOCK}
+_PRECOND = {"jacobi": L.PRECOND_JACOBI, "block": L.PRECOND_NODE_BLOCK, "multigrid": L.PRECOND_MULTIGRID}
 
 
 def _f64(a):
@@ -29,7 +29,7 @@ def _p(a, ct):
     return None if a is None else a.ctypes.data_as(C.POINTER(ct))
 
 
-def make_options(precision="fp64", precond="block", newton_tol=1e-8, krylov_rtol=None, max_newton=50,
+def make_options(precision="fp64", precond="multigrid", newton_tol=1e-8, krylov_rtol=None, max_newton=50,
                  max_krylov=5000, max_halvings=6, krylov_blocks=0, gmres_m=64, krylov="bicgstab",
                  wait_limit_s=2.0):
     o = L.Options()

@@ -57,7 +57,7 @@ def _compare(lib, p, seeds, damaged, rtol, tol):
     """Solve the same assembled systems with lgdm_solve (workspace) and with
     lgdm_solve_noalloc (static array), calls in a row, and compare."""
     from paper_2301_06503_gb300 import Sim
-    s = Sim(p.mesh, p.material, p.bcs, krylov_rtol=rtol)
+    s = Sim(p.mesh, p.material, p.bcs, krylov_rtol=rtol, precond="block")   # the entry point's preconditioner
     stream = torch.cuda.current_stream()
     for seed in seeds:
         u, kh = _state(p, seed, damaged)
