@@ -1,26 +1,29 @@
 #!/usr/bin/env python
 """Throughput of the LGDM hot path on GB300.
 
-Workload: the notched plate (200 x 200 four-node quads, plane strain, 40k
-elements, 160k Gauss points, 121k dofs).  A timed step solves one load
-increment (0.1 mm / 500) from the initial state: device-side reset of the
-state, the Dirichlet predictor, Newton iterations until convergence -- each
-one element integration at every Gauss point, deterministic CSR assembly
-with Dirichlet rows, node-block Jacobi set-up, and one persistent BiCGSTAB
-launch with the fused update and convergence test -- then the history commit
-and the reaction.  The metric counts Gauss-point integrations with assembly:
-every Newton iteration integrates nel * ngp points.  Inputs are resident in
-HBM when the timed region starts; L2 is flushed (256 MB write) before each
-step.  The e2e figure drives the same step through the public API from
-pinned host buffers (state in, damage field and reaction out).
+Default workload: the batch of 256 notched plates (20..300 four-node quads
+per edge, seeded draw; 4.84M elements, 19.4M Gauss points, 14.6M dofs) with
+the FP32 tangent and FP64 residual, in one batch: persistent element kernel,
+batched gather and preconditioner set-up, grouped multigrid-preconditioned
+BiCGSTAB solves, the batched update, autotuned tiles.  A timed step is one
+batched Newton iteration of every member at load increment 1 from its
+initial state (device-side reset, Dirichlet predictor, assembly, multigrid
+set-up, solve, update and convergence test).
 
-Other workloads (--workload): bar (100 two-node elements), beam (200 x 40 x
-40 hexahedra, 1.35M dofs), batch (256 notched plates of 20..300 elements per
-edge in one batch, 4.84M elements: persistent element kernel, grouped
-solves, autotuned tiles; a step is one batched Newton iteration of all of
-them at load increment 1 -- assembly, solve, update -- and the phase timers
-run the batch without its CUDA graph).  --precision fp32 assembles the tangent and applies the
-preconditioner in FP32 (residual, inner products and tests in FP64).
+The metric counts Gauss-point integrations with assembly per second: the
+Gauss points integrated in the timed region over the CUDA-event time of the
+element-integration and CSR-gather (with Dirichlet rows) launches in it.
+The line also gives the whole step's rate (same Gauss points over the whole
+step time), the rooflines of the element and Krylov kernels, the oracle on
+the host cores (one core and all cores) and an end-to-end figure through the
+public API from pinned host buffers (state in, damage field and reaction
+out).  Inputs are resident in HBM when the timed region starts; L2 is flushed
+(256 MB write) before each step and the batch's state is far larger than L2.
+
+Other workloads (--workload): plate (the 200 x 200 notched plate), bar (100
+two-node elements), beam (200 x 40 x 40 hexahedra, 1.35M dofs); for them a
+step solves load increment 1 (Newton to convergence) unless --mode newton.
+--precision fp64 assembles and applies everything in FP64.
 
 --serving runs the request-serving comparison instead and prints its own
 JSON line: the first --requests requests of the seeded Poisson trace (70 %
@@ -56,8 +59,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
-    ap.add_argument("--workload", default="plate", choices=["plate", "bar", "beam", "batch"])
+    ap.add_argument("--precision", default=None, choices=["fp64", "fp32"],
+                    help="fp32: FP32 tangent, FP64 residual (default for the batch); fp64 (default otherwise)")
+    ap.add_argument("--workload", default="batch", choices=["plate", "bar", "beam", "batch"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--mode", default=None, choices=["loadstep", "newton"],
                     help="loadstep: a step is a converged load increment (default for one simulation); "
@@ -83,6 +87,11 @@ def workload(name):
     if name == "beam":
         return [li.tpb_beam_problem()], "tpb_beam_h8_200x40x40"
     return li.batch_plate_problems(), "batch_plates_q4_20to300"
+
+
+def mg_levels(sz):
+    """[(nodes, node pairs)] of the multigrid levels of a simulation (empty without)."""
+    return [(int(sz.mg_nnode[k]), int(sz.mg_npairs[k])) for k in range(int(sz.mg_levels))]
 
 
 def dist_env():
@@ -189,59 +198,97 @@ def _cores_used(cpu_s, wall_s):
     return max(1, int(round(cpu_s / wall_s))) if wall_s > 0 else 1
 
 
-def cpu_baseline(problems, label, newton_iters=2, budget_s=15.0):
-    """The oracle as it stands: the first Newton iterations of load step 1 of
-    each problem in turn until about budget_s of CPU work (bounded sample)."""
+def _problem_list(workload_name, count):
+    """The problems of a workload, rebuilt from its seeded recipe (no arrays pass between processes)."""
+    import lgdm_inputs as li
+    if workload_name == "batch":
+        return li.batch_plate_problems()[:count]
+    return workload(workload_name)[0]
+
+
+def _oracle_assembly(workload_name, count, first, stride, budget_s):
+    """Time the oracle's assembly (element integration of every Gauss point,
+    sparse assembly, Dirichlet rows) at load step 1 from the initial state,
+    on problems first, first+stride, ... (cycling) until budget_s of wall
+    time.  Returns (Gauss points, wall seconds, CPU seconds, assemblies)."""
     from oracle import assembly as asm
     from oracle import newton as nw
-    import scipy.sparse.linalg as spla
-    gp, done = 0, 0
+    probs = _problem_list(workload_name, count)
+    gp = done = 0
+    k = first
     c0, t0 = time.process_time(), time.perf_counter()
-    for problem in problems:
-        st = nw.initial_state(problem)
+    while True:
+        p = probs[k % len(probs)]
+        st = nw.initial_state(p)
         u = st.u.copy()
-        u[problem.bcs.dir_dof] = problem.bcs.dir_scale * problem.load(1)
-        for _ in range(newton_iters):
-            K, r = asm.assemble(problem.mesh, problem.material, u, st.kappa_hist)
-            Kb, rb = asm.apply_dirichlet(K, r, problem.bcs.dir_dof)
-            u += spla.spsolve(Kb.tocsc(), -rb)
-        gp += newton_iters * problem.mesh.nel * problem.mesh.ngp
+        u[p.bcs.dir_dof] = p.bcs.dir_scale * p.load(1)
+        K, r = asm.assemble(p.mesh, p.material, u, st.kappa_hist)
+        asm.apply_dirichlet(K, r, p.bcs.dir_dof)
+        gp += p.mesh.nel * p.mesh.ngp
         done += 1
+        k += stride
         if time.perf_counter() - t0 > budget_s:
             break
-    dt = time.perf_counter() - t0
-    cpu_s = time.process_time() - c0
-    return {"value": gp / dt, "unit": UNIT, "cores": _cores_used(cpu_s, dt), "kind": "oracle",
-            "sample": f"{label}: first {newton_iters} Newton iterations of load step 1 of {done} of "
-                      f"{len(problems)} simulation(s) (numpy element integration + scipy SuperLU direct "
-                      f"solve), {dt:.1f} s wall, {cpu_s:.1f} s CPU"}
+    return gp, time.perf_counter() - t0, time.process_time() - c0, done
+
+
+def _host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def cpu_baseline(workload_name, count, label, budget_s=8.0):
+    """The oracle as it stands, on the same metric: Gauss-point integrations
+    with assembly per second.  One process (one core) and a pool of spawned
+    processes over all host cores, each assembling different problems of the
+    workload for about budget_s (a bounded sample)."""
+    import multiprocessing as mp
+    gp1, wall1, cpu1, n1 = _oracle_assembly(workload_name, count, 0, 1, budget_s)
+    one = {"value": gp1 / wall1, "unit": UNIT, "cores": _cores_used(cpu1, wall1), "kind": "oracle",
+           "sample": f"{label}: {n1} oracle assemblies (numpy element integration, scipy sparse assembly, "
+                     f"Dirichlet rows) at load step 1, {wall1:.1f} s wall"}
+    ncores = _host_cores()
+    ctx = mp.get_context("spawn")
+    t0 = time.perf_counter()
+    with ctx.Pool(ncores) as pool:
+        res = pool.starmap(_oracle_assembly, [(workload_name, count, w, ncores, budget_s) for w in range(ncores)])
+    wall = time.perf_counter() - t0
+    gp = sum(r[0] for r in res)
+    span = max(r[1] for r in res)
+    cpu = sum(r[2] for r in res)
+    n = sum(r[3] for r in res)
+    return {"value": gp / span, "unit": UNIT, "cores": _cores_used(cpu, span), "kind": "oracle",
+            "sample": f"{label}: {n} oracle assemblies at load step 1 in {ncores} spawned processes (each "
+                      f"assembling different problems for {budget_s:.0f} s; throughput = Gauss points / "
+                      f"longest worker time {span:.1f} s; pool wall {wall:.1f} s with start-up)",
+            "one_core": one}
 
 
 def run_reference(args):
-    """Reference arm: the CPU oracle, one Newton iteration per step (bounded sample)."""
+    """Reference arm: the CPU oracle on the same metric (Gauss-point
+    integrations with assembly per second); a step is one oracle assembly of
+    the next problem of the workload (bounded sample)."""
     world, rank, _ = dist_env()
     if rank != 0:
         return
     from oracle import assembly as asm
     from oracle import newton as nw
-    import numpy as np
-    import scipy.sparse.linalg as spla
     probs, label = workload(args.workload)
-    # one Newton iteration per step; the batch workload cycles through its plates
-    states = []
-    for p in probs:
-        st = nw.initial_state(p)
-        u0 = st.u.copy()
-        u0[p.bcs.dir_dof] = p.bcs.dir_scale * p.load(1)
-        states.append((p, u0, st.kappa_hist))
+    if args.workload == "batch":
+        probs = probs[:args.batch_count]
+        label = f"batch_{len(probs)}_plates_q4_20to300"
     k = [0]
 
     def step():
-        p, u0, kh = states[k[0] % len(states)]
+        p = probs[k[0] % len(probs)]
         k[0] += 1
-        K, r = asm.assemble(p.mesh, p.material, u0, kh)
-        Kb, rb = asm.apply_dirichlet(K, r, p.bcs.dir_dof)
-        du = spla.spsolve(Kb.tocsc(), -rb)
+        st = nw.initial_state(p)
+        u = st.u.copy()
+        u[p.bcs.dir_dof] = p.bcs.dir_scale * p.load(1)
+        K, r = asm.assemble(p.mesh, p.material, u, st.kappa_hist)
+        asm.apply_dirichlet(K, r, p.bcs.dir_dof)
         return p.mesh.nel * p.mesh.ngp
 
     for _ in range(args.warmup):
@@ -260,10 +307,11 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wall / len(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": label, "step": "one Newton iteration (assemble + direct solve) at load step 1",
+            "config": {"workload": label, "step": "one oracle assembly (element integration, sparse assembly, "
+                                                  "Dirichlet rows) of the next problem at load step 1",
                        "l2": "n/a (CPU)"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": f"{label}: {args.steps} Newton iterations at load step 1"},
+                             "sample": f"{label}: {args.steps} oracle assemblies, problems in order"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -306,7 +354,7 @@ class SingleLeg:
                 "elements": m.nel, "elem": m.elem, "nnode": int(sz.nnode), "nel": m.nel, "nd": int(sz.nd),
                 "nnz": int(sz.nnz), "npairs": int(sz.npairs),
                 "members": [(int(sz.nnode), int(sz.nd), int(sz.nnz), int(sz.npairs),
-                             c1["krylov_iters"] - self.c0["krylov_iters"])]}
+                             c1["krylov_iters"] - self.c0["krylov_iters"], mg_levels(sz))]}
 
     def e2e(self, reps):
         import torch
@@ -383,7 +431,8 @@ class BatchLeg:
                 "nd": int(self.sims[0].sizes.nd), "nnz": sum(int(s.sizes.nnz) for s in self.sims),
                 "npairs": sum(int(s.sizes.npairs) for s in self.sims), "tuning": self.tuning,
                 "members": [(int(s.sizes.nnode), int(s.sizes.nd), int(s.sizes.nnz), int(s.sizes.npairs),
-                             b["krylov_iters"] - a["krylov_iters"]) for s, a, b in zip(self.sims, self.c0, c1)]}
+                             b["krylov_iters"] - a["krylov_iters"], mg_levels(s.sizes))
+                            for s, a, b in zip(self.sims, self.c0, c1)]}
 
     def e2e(self, reps):
         import torch
@@ -467,6 +516,7 @@ def run_ours(args):
     st = leg.stop_timing()
     t_s = sum(step_ms) / 1e3
     t_job, gp_job = job_totals(t_s, st["gp"], world, "cuda")
+    t_asm_job, _ = job_totals((st["phase_ms"]["element"] + st["phase_ms"]["gather"]) * 1e-3, 0, world, "cuda")
     e2e = leg.e2e(max(1, min(args.steps, 3))) if rank == 0 else None
     meshes = leg.meshes
     leg.close()
@@ -474,24 +524,24 @@ def run_ours(args):
         return
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(probs, label)
-    line = summarize(args, label, len(probs), meshes, st, step_ms, t_job, gp_job, world, peaks(), e2e, cpu, ck)
+        cpu = cpu_baseline(args.workload, len(probs), label)
+    line = summarize(args, label, len(probs), meshes, st, step_ms, t_job, gp_job, world, peaks(), e2e, cpu, ck,
+                     t_asm_job)
     print(json.dumps(line), flush=True)
 
 
-def summarize(args, label, n_sims, meshes, st, step_ms, t_job, gp_job, world, pk, e2e, cpu, ck):
+def summarize(args, label, n_sims, meshes, st, step_ms, t_job, gp_job, world, pk, e2e, cpu, ck, t_asm_job=None):
     """The JSON line of one timed run: throughput, rooflines of the element
     and Krylov kernels (work over the timed region's CUDA-event phase times),
     the assembly-only rate and the details."""
     from paper_2301_06503_gb300 import roofline
-    value = gp_job / t_job
     fp32 = args.precision == "fp32"
     tb = 4 if fp32 else 8
     phase_ms, phase_n = st["phase_ms"], st["phase_n"]
     # Krylov work summed member by member: iterations x work per iteration
     kr_flops = kr_bytes = 0
-    for nnode, nd, nnz, npairs, its in st["members"]:
-        f1, b1 = roofline.krylov_iteration(nnode, nd, nnz, npairs, tb)
+    for nnode, nd, nnz, npairs, its, levels in st["members"]:
+        f1, b1 = roofline.krylov_iteration(nnode, nd, nnz, npairs, tb, levels)
         kr_flops += f1 * its
         kr_bytes += b1 * its
     res_f, tan_f = roofline.element_flops(st["elem"])
@@ -549,8 +599,13 @@ def summarize(args, label, n_sims, meshes, st, step_ms, t_job, gp_job, world, pk
     roof_kr["traffic"] = (tr * its_per_launch) if tr is not None else None
     roof_dom = roof_kr if phase_ms["krylov"] >= phase_ms["element"] else roof_el
 
-    asm_total_ms = sum(phase_ms[k] for k in ("element", "gather", "precond"))
-    asm_rate = st["gp"] / (asm_total_ms * 1e-3) if asm_total_ms > 0 else None
+    # the metric: Gauss points over the element-integration and
+    # scatter (CSR gather with the Dirichlet rows) time inside the timed
+    # region; replicas: every rank's points over the slowest rank's time
+    if t_asm_job is None:
+        t_asm_job = (phase_ms["element"] + phase_ms["gather"]) * 1e-3
+    value = gp_job / t_asm_job if t_asm_job > 0 else None
+    setup_ms = phase_ms.get("precond", 0.0)
     return {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * t_job / args.steps, "higher_is_better": True,
@@ -564,14 +619,14 @@ def summarize(args, label, n_sims, meshes, st, step_ms, t_job, gp_job, world, pk
                    "l2": "flushed (256 MB write) before every step", "parallelism": f"replicas x{world}"},
         "roofline": roof_dom, "roofline_element": roof_el, "roofline_krylov": roof_kr,
         "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(st["launches"]), "clocks": ck,
-        # the same Gauss points over the assembly kernels' own time (element integration, CSR gather
-        # with Dirichlet rows, preconditioner set-up), CUDA events inside the timed region
-        "assembly_only": {"value": asm_rate, "unit": UNIT,
-                          "definition": "Gauss points integrated in the timed region / the summed time of "
-                                        "the element, gather and preconditioner launches"},
+        "value_definition": "Gauss points integrated in the timed region / the summed CUDA-event time of the "
+                            "element-integration and CSR-gather (+ Dirichlet rows) launches in it",
+        # the whole step: assembly, preconditioner set-up, Krylov solve and update
+        "whole_step": {"value": gp_job / t_job, "unit": UNIT, "ms_per_step": 1e3 * t_job / args.steps,
+                       "definition": "Gauss points integrated / device time of the whole steps"},
         "detail": {"newton_iters": st["newton"], "krylov_iters": st["krylov_iters"], "halvings": st["halvings"],
                    "phase_ms": phase_ms, "phase_launches": phase_n, "element_ms_per_launch": el_ms,
-                   "assembly_gp_per_s": asm_rate, "step_ms": step_ms,
+                   "preconditioner_setup_ms": setup_ms, "step_ms": step_ms,
                    **({"tuning": st["tuning"]} if "tuning" in st else {})},
     }
 
@@ -621,6 +676,8 @@ def run_serving(args):
 
 def main():
     args = parse()
+    if args.precision is None:
+        args.precision = "fp32" if args.workload == "batch" else "fp64"
     if args.mode is None:
         args.mode = "newton" if args.workload == "batch" else "loadstep"
     if args.serving:

@@ -131,12 +131,18 @@ typedef struct {
 
 typedef struct lgdm_sim lgdm_sim;
 
-/* Sizes of a created simulation. */
+/* Sizes of a created simulation.  mg_levels: levels of the multigrid
+ * preconditioner (0 without it); mg_nnode / mg_npairs: nodes and node pairs
+ * of each level (level 0 is the system itself). */
+#define LGDM_MG_MAX_LEVELS 10
 typedef struct {
   int32_t dim, nen, ngp, nd;
   int32_t nnode, nelem;
   int64_t ndof, nnz, npairs;  /* npairs: node pairs sharing an element */
   size_t workspace_bytes;
+  int32_t mg_levels;
+  int32_t mg_nnode[LGDM_MG_MAX_LEVELS];
+  int64_t mg_npairs[LGDM_MG_MAX_LEVELS];
 } lgdm_sizes;
 
 int32_t lgdm_abi_version(void);
@@ -339,6 +345,14 @@ const char *lgdm_batch_last_error(const lgdm_batch *batch);
 lgdm_status lgdm_batch_set_tuning(lgdm_batch *batch, int32_t block_threads, int32_t grid_factor, int32_t use_graph);
 lgdm_status lgdm_batch_get_tuning(const lgdm_batch *batch, int32_t *block_threads, int32_t *grid_factor,
                                   int32_t *graph_in_use);
+/* Solve tuning: each member's Krylov launch group gets about
+ * nodes_per_block nodes per block (default 4096; at least the blocks its
+ * reduction tiles need, at most one per tile); members of the same nd are
+ * packed, largest first, into co-resident cooperative launches ("waves")
+ * that run one after the other.  Results do not depend on this setting.
+ * get returns the setting and the number of waves. */
+lgdm_status lgdm_batch_set_solve_tuning(lgdm_batch *batch, int32_t nodes_per_block);
+lgdm_status lgdm_batch_get_solve_tuning(const lgdm_batch *batch, int32_t *nodes_per_block, int32_t *waves);
 /* Autotuner: times the batched assembly for every block size and grid factor
  * with CUDA events on the current states and keeps the fastest. */
 lgdm_status lgdm_batch_autotune(lgdm_batch *batch, int32_t *block_threads, int32_t *grid_factor, double *ms);

@@ -53,7 +53,8 @@ class Options(C.Structure):
 class Sizes(C.Structure):
     _fields_ = [("dim", C.c_int32), ("nen", C.c_int32), ("ngp", C.c_int32), ("nd", C.c_int32),
                 ("nnode", C.c_int32), ("nelem", C.c_int32), ("ndof", C.c_int64), ("nnz", C.c_int64),
-                ("npairs", C.c_int64), ("workspace_bytes", C.c_size_t)]
+                ("npairs", C.c_int64), ("workspace_bytes", C.c_size_t), ("mg_levels", C.c_int32),
+                ("mg_nnode", C.c_int32 * 10), ("mg_npairs", C.c_int64 * 10)]
 
 
 class LgdmError(RuntimeError):
@@ -103,6 +104,8 @@ _SIGS = {
     "lgdm_batch_last_error": (C.c_char_p, [C.c_void_p]),
     "lgdm_batch_set_tuning": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_int32]),
     "lgdm_batch_get_tuning": (C.c_int, [C.c_void_p, _ip, _ip, _ip]),
+    "lgdm_batch_set_solve_tuning": (C.c_int, [C.c_void_p, C.c_int32]),
+    "lgdm_batch_get_solve_tuning": (C.c_int, [C.c_void_p, _ip, _ip]),
     "lgdm_batch_autotune": (C.c_int, [C.c_void_p, _ip, _ip, _dp]),
     "lgdm_batch_assemble": (C.c_int, [C.c_void_p, _ip]),
     "lgdm_batch_enable_timers": (C.c_int, [C.c_void_p, C.c_int32]),

@@ -56,6 +56,14 @@ class Batch:
         self._ck(self._lib.lgdm_batch_get_tuning(self.h, C.byref(bt), C.byref(gf), C.byref(g)))
         return {"block_threads": bt.value, "grid_factor": gf.value, "graph": int(g.value)}
 
+    def set_solve_tuning(self, nodes_per_block=4096):
+        self._ck(self._lib.lgdm_batch_set_solve_tuning(self.h, int(nodes_per_block)))
+
+    def solve_tuning(self):
+        npb, w = C.c_int32(), C.c_int32()
+        self._ck(self._lib.lgdm_batch_get_solve_tuning(self.h, C.byref(npb), C.byref(w)))
+        return {"nodes_per_block": npb.value, "waves": w.value}
+
     def autotune(self):
         bt, gf, ms = C.c_int32(), C.c_int32(), C.c_double()
         self._ck(self._lib.lgdm_batch_autotune(self.h, C.byref(bt), C.byref(gf), C.byref(ms)))

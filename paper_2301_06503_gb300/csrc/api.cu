@@ -798,6 +798,11 @@ lgdm_status lgdm_get_sizes(const lgdm_sim *s, lgdm_sizes *o) {
   o->nnz = s->nnz;
   o->npairs = s->npairs;
   o->workspace_bytes = s->ws_needed;
+  o->mg_levels = s->amg_levels;
+  for (int l = 0; l < LGDM_MG_MAX_LEVELS; ++l) {
+    o->mg_nnode[l] = l < s->amg_levels ? s->h_lev[l].nnode : 0;
+    o->mg_npairs[l] = l < s->amg_levels ? s->h_lev[l].npairs : 0;
+  }
   return LGDM_OK;
 }
 
@@ -1425,6 +1430,10 @@ struct lgdm_batch {
     int blocks = 0;
   };
   std::vector<Wave> waves;
+  int32_t *d_wave_members = nullptr;   // [n] members of all waves, wave after wave
+  int32_t *d_wave_start = nullptr;     // [2n] block-group starts of all waves
+  int nodes_per_block = 4096;          // solve tuning: target nodes per Krylov block
+  std::vector<int32_t> h_wave_members, h_wave_start;
   int bt = 128, grid_factor = 2, sms = 152;
   bool graph_on = true, graph_ok = false, graph_tried = false;
   int graph_mode = 0;                  // 0 none, 1 assembly launches, 2 assembly and solve
@@ -1477,6 +1486,92 @@ lgdm_status bfail(lgdm_batch *b, lgdm_status st, const std::string &m) {
   do {                                                                    \
     if ((b)->timers_on) LGDM_BCUDA(b, cudaEventRecord((b)->tev[k], (b)->stream)); \
   } while (0)
+
+// Solve waves: the members of one nd are given block groups of about
+// nodes_per_block nodes per block (at least their fewest, at most one block
+// per reduction tile), then packed, largest first, into co-resident
+// cooperative launches (first fit); the blocks a wave has left over are
+// shared out in proportion to node counts.  The waves run one after the
+// other.  A member's result does not depend on its group size (tile-ordered
+// inner products, per-node multigrid arithmetic).
+lgdm_status build_waves(lgdm_batch *b, int nodes_per_block) {
+  const int cap = b->fp32 ? bicgstab_grouped_max_blocks<float>() : bicgstab_grouped_max_blocks<double>();
+  const int n = b->n;
+  b->waves.clear();
+  b->h_wave_start.clear();
+  for (int nd = 2; nd <= 4; ++nd) {
+    std::vector<int32_t> ms;
+    for (int i = 0; i < n; ++i)
+      if (b->sims[i]->nd == nd) ms.push_back(i);
+    std::stable_sort(ms.begin(), ms.end(), [&](int32_t x, int32_t y) { return b->sims[x]->nnode > b->sims[y]->nnode; });
+    std::vector<std::vector<int32_t>> wm;
+    std::vector<std::vector<int64_t>> wb;
+    std::vector<int64_t> used;
+    for (int32_t i : ms) {
+      lgdm_sim *s = b->sims[i];
+      const int64_t lo = std::max<int64_t>(1, krylov_min_blocks(s->nnode));
+      if (lo > cap) return bfail(b, LGDM_ERR_INVALID_ARG, "member Krylov grid too large");
+      const int64_t hi = std::max<int64_t>(lo, std::min<int64_t>(krylov_ntiles(s->nnode), cap));
+      const int64_t want = std::min(hi, std::max(lo, ((int64_t)s->nnode + nodes_per_block - 1) / nodes_per_block));
+      size_t w = 0;
+      while (w < used.size() && used[w] + want > cap) ++w;
+      if (w == used.size()) {
+        wm.emplace_back();
+        wb.emplace_back();
+        used.push_back(0);
+      }
+      wm[w].push_back(i);
+      wb[w].push_back(want);
+      used[w] += want;
+    }
+    for (size_t w = 0; w < wm.size(); ++w) {
+      // share the left-over blocks in proportion to node counts, up to each member's maximum
+      int64_t nodes = 0;
+      for (int32_t i : wm[w]) nodes += b->sims[i]->nnode;
+      int64_t spare = cap - used[w];
+      for (size_t j = 0; j < wm[w].size() && spare > 0; ++j) {
+        lgdm_sim *s = b->sims[wm[w][j]];
+        const int64_t hi = std::min<int64_t>(krylov_ntiles(s->nnode), cap);
+        const int64_t add = std::min<int64_t>(
+            {spare, std::max<int64_t>(0, hi - wb[w][j]),
+             (int64_t)((double)(cap - used[w]) * (double)s->nnode / (double)std::max<int64_t>(nodes, 1))});
+        wb[w][j] += add;
+        spare -= add;
+      }
+      lgdm_batch::Wave wv;
+      wv.nd = nd;
+      // members in index order inside the wave
+      std::vector<size_t> ord(wm[w].size());
+      for (size_t j = 0; j < ord.size(); ++j) ord[j] = j;
+      std::sort(ord.begin(), ord.end(), [&](size_t x, size_t y) { return wm[w][x] < wm[w][y]; });
+      std::vector<int32_t> st(1, 0);
+      for (size_t j : ord) {
+        wv.members.push_back(wm[w][j]);
+        st.push_back(st.back() + (int32_t)wb[w][j]);
+      }
+      wv.blocks = st.back();
+      b->waves.push_back(std::move(wv));
+      b->waves.back().d_start = nullptr;
+      b->h_wave_start.insert(b->h_wave_start.end(), st.begin(), st.end());
+    }
+  }
+  // device copies: members wave after wave, block starts wave after wave
+  b->h_wave_members.clear();
+  size_t mo = 0, so = 0;
+  for (auto &w : b->waves) {
+    w.d_members = b->d_wave_members + mo;
+    w.d_start = b->d_wave_start + so;
+    b->h_wave_members.insert(b->h_wave_members.end(), w.members.begin(), w.members.end());
+    mo += w.members.size();
+    so += w.members.size() + 1;
+  }
+  LGDM_BCUDA(b, cudaMemcpyAsync(b->d_wave_members, b->h_wave_members.data(), sizeof(int32_t) * mo,
+                                cudaMemcpyHostToDevice, b->stream));
+  LGDM_BCUDA(b, cudaMemcpyAsync(b->d_wave_start, b->h_wave_start.data(), sizeof(int32_t) * so, cudaMemcpyHostToDevice,
+                                b->stream));
+  LGDM_BCUDA(b, cudaStreamSynchronize(b->stream));
+  return LGDM_OK;
+}
 
 // The launches of one batched Newton step up to the solve (mode 0): the
 // element launches of every element-type group, then the gathers, then the
@@ -1725,61 +1820,11 @@ lgdm_status lgdm_batch_create(lgdm_sim *const *sims, int32_t n, void *ws, size_t
       LGDM_BCUDA(b, cudaMemcpyAsync(g.d_gblock, gb.data(), sizeof(int64_t) * (m + 1), cudaMemcpyHostToDevice, b->stream));
       LGDM_BCUDA(b, cudaMemcpyAsync(g.d_pblock, pbk.data(), sizeof(int64_t) * (m + 1), cudaMemcpyHostToDevice, b->stream));
     }
-    // waves: members with the same nd that fit one co-resident launch
-    // together (each at least its fewest blocks); a wave's blocks are then
-    // shared out in proportion to the members' node counts, so that every
-    // member runs with about the same nodes per thread.  A member's result
-    // does not depend on its block count (tile reductions).
-    const int cap = b->fp32 ? bicgstab_grouped_max_blocks<float>() : bicgstab_grouped_max_blocks<double>();
-    for (int nd = 2; nd <= 4; ++nd) {
-      lgdm_batch::Wave w;
-      w.nd = nd;
-      int64_t minsum = 0;
-      for (int i = 0; i < n; ++i) {
-        lgdm_sim *s = b->sims[i];
-        if (s->nd != nd) continue;
-        const int64_t mb = std::max<int64_t>(1, krylov_min_blocks(s->nnode));
-        if (mb > cap) { delete b; return fail(nullptr, LGDM_ERR_INVALID_ARG, "member Krylov grid too large"); }
-        if (minsum + mb > cap) {
-          b->waves.push_back(w);
-          w = lgdm_batch::Wave();
-          w.nd = nd;
-          minsum = 0;
-        }
-        w.members.push_back(i);
-        minsum += mb;
-      }
-      if (!w.members.empty()) b->waves.push_back(w);
-    }
-    for (auto &w : b->waves) {
-      const int m = (int)w.members.size();
-      int64_t nodes = 0;
-      for (int j = 0; j < m; ++j) nodes += b->sims[w.members[j]]->nnode;
-      std::vector<int64_t> nbk(m), lo(m);
-      int64_t sum = 0;
-      for (int j = 0; j < m; ++j) {
-        lgdm_sim *s = b->sims[w.members[j]];
-        lo[j] = std::max<int64_t>(1, krylov_min_blocks(s->nnode));
-        const int64_t hi = std::max<int64_t>(lo[j], std::min<int64_t>(s->krylov_blocks, krylov_ntiles(s->nnode)));
-        const int64_t share = (int64_t)((double)cap * (double)s->nnode / (double)std::max<int64_t>(nodes, 1));
-        nbk[j] = std::min(hi, std::max(lo[j], share));
-        sum += nbk[j];
-      }
-      while (sum > cap) {                    // trim the largest groups down to their minimum
-        int jm = -1;
-        for (int j = 0; j < m; ++j)
-          if (nbk[j] > lo[j] && (jm < 0 || nbk[j] > nbk[jm])) jm = j;
-        if (jm < 0) break;
-        --nbk[jm];
-        --sum;
-      }
-      std::vector<int32_t> st(m + 1, 0);
-      for (int j = 0; j < m; ++j) st[j + 1] = st[j] + (int32_t)nbk[j];
-      w.blocks = st[m];
-      w.d_members = c.take<int32_t>(m);
-      w.d_start = c.take<int32_t>(m + 1);
-      LGDM_BCUDA(b, cudaMemcpyAsync(w.d_members, w.members.data(), sizeof(int32_t) * m, cudaMemcpyHostToDevice, b->stream));
-      LGDM_BCUDA(b, cudaMemcpyAsync(w.d_start, st.data(), sizeof(int32_t) * (m + 1), cudaMemcpyHostToDevice, b->stream));
+    b->d_wave_members = c.take<int32_t>(n);
+    b->d_wave_start = c.take<int32_t>(2 * (size_t)n);
+    {
+      const lgdm_status wst = build_waves(b, b->nodes_per_block);
+      if (wst != LGDM_OK) { const std::string m = b->err; delete b; return fail(nullptr, wst, m); }
     }
     if (c.off > ws_bytes) { delete b; return fail(nullptr, LGDM_ERR_OOM, "batch workspace too small"); }
     LGDM_BCUDA(b, cudaMemcpyAsync(b->d_sims, hs.data(), sizeof(BatchSim) * n, cudaMemcpyHostToDevice, b->stream));
@@ -1831,6 +1876,25 @@ lgdm_status lgdm_batch_set_tuning(lgdm_batch *b, int32_t block_threads, int32_t 
     LGDM_BCUDA(b, cudaMemcpyAsync(g.d_tile, tl.data(), sizeof(int64_t) * (m + 1), cudaMemcpyHostToDevice, b->stream));
   }
   LGDM_BCUDA(b, cudaStreamSynchronize(b->stream));
+  return LGDM_OK;
+}
+
+lgdm_status lgdm_batch_set_solve_tuning(lgdm_batch *b, int32_t nodes_per_block) {
+  if (!b || nodes_per_block < 32 || nodes_per_block > (1 << 20))
+    return bfail(b, LGDM_ERR_INVALID_ARG, "nodes_per_block must be in 32 .. 2^20");
+  b->nodes_per_block = nodes_per_block;
+  if (b->graph) cudaGraphExecDestroy(b->graph);       // the waves are baked into the captured graph
+  b->graph = nullptr;
+  b->graph_ok = b->graph_tried = false;
+  b->graph_mode = 0;
+  b->direct_issues = 0;
+  return build_waves(b, nodes_per_block);
+}
+
+lgdm_status lgdm_batch_get_solve_tuning(const lgdm_batch *b, int32_t *nodes_per_block, int32_t *waves) {
+  if (!b) return fail(nullptr, LGDM_ERR_INVALID_ARG, "NULL batch");
+  if (nodes_per_block) *nodes_per_block = b->nodes_per_block;
+  if (waves) *waves = (int32_t)b->waves.size();
   return LGDM_OK;
 }
 

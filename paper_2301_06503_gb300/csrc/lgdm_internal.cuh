@@ -132,7 +132,7 @@ cudaError_t launch_damaged_volume(int elem, const MeshView &m, const MatConst &m
 // aggregate's nd values to each of its nodes, the restriction sums them, and
 // the level-(l+1) matrix is the Galerkin product R A_l P: every block of it is
 // the fixed-order sum of the level-l blocks of the node pairs that map to it.
-constexpr int AMG_MAX_LEVELS = 10;
+constexpr int AMG_MAX_LEVELS = LGDM_MG_MAX_LEVELS;
 constexpr int AMG_COARSE_MAX = 24;        // nodes of the coarsest level (dense inverse)
 constexpr int AMG_SINGLE_BLOCK = 2048;    // levels with at most this many nodes run in one block
 constexpr double AMG_OMEGA = 0.7;         // damping of the block-Jacobi smoother

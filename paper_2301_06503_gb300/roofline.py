@@ -47,12 +47,46 @@ def assembly_bytes(elem: int, nnode: int, nel: int, nnz: int, tangent_bytes: int
     return reads + writes
 
 
-def krylov_iteration(nnode: int, nd: int, nnz: int, npairs: int, tangent_bytes: int):
-    """(flops, bytes) of one BiCGSTAB iteration: 2 SpMV, 2 block-Jacobi applies,
-    4 inner products and 6 vector updates."""
+def _spmv(nnode, nd, npairs, tb):
+    """(flops, bytes) of y = A x on a node-block CSR level: nd*nd values per
+    node pair, one neighbour index per pair, x read and y written once."""
+    nnz = nd * nd * npairs
+    return 2 * nnz, nnz * tb + npairs * 4 + (nnode + 1) * 4 + 2 * nd * nnode * 8
+
+
+def _jacobi(nnode, nd, tb):
+    """(flops, bytes) of one node-block Jacobi apply."""
+    return 2 * nnode * nd * nd, nnode * nd * nd * tb + 2 * nd * nnode * 8
+
+
+def vcycle(levels, nd, tb):
+    """(flops, bytes) of one multigrid V-cycle; levels = [(nnode, npairs), ...]
+    from the finest: per level above the coarsest a Jacobi pre-smoothing, a
+    residual (SpMV), the restriction sum, and the post-smoothing (SpMV on the
+    prolonged iterate, Jacobi apply, update); the coarsest a dense N x N
+    product (N = nd * its nodes)."""
+    f = b = 0
+    for n, np_ in levels[:-1]:
+        fj, bj = _jacobi(n, nd, tb)
+        fs, bs = _spmv(n, nd, np_, tb)
+        f += 2 * fj + 2 * fs + 4 * nd * n
+        b += 2 * bj + 2 * bs + 6 * nd * n * 8 + n * 8
+    nc = nd * levels[-1][0]
+    f += 2 * nc * nc
+    b += nc * nc * 8 + 2 * nc * 8
+    return f, b
+
+
+def krylov_iteration(nnode: int, nd: int, nnz: int, npairs: int, tangent_bytes: int, levels=None):
+    """(flops, bytes) of one BiCGSTAB iteration: 2 SpMV, 2 preconditioner
+    applies (node-block Jacobi, or a multigrid V-cycle when ``levels`` lists
+    the multigrid levels), 4 inner products and 6 vector updates."""
     ndof = nd * nnode
-    flops = 2 * (2 * nnz) + 2 * (2 * nnode * nd * nd) + 2 * 4 * ndof + 2 * 8 * ndof
-    spmv = nnz * tangent_bytes + npairs * 4 + (nnode + 1) * 4 + ndof * tangent_bytes + ndof * 8
-    prec = nnode * nd * nd * tangent_bytes + ndof * (8 + 8 + tangent_bytes)
+    fs, bs = _spmv(nnode, nd, npairs, tangent_bytes)
+    if levels and len(levels) > 1:
+        fp, bp = vcycle(levels, nd, tangent_bytes)
+    else:
+        fp, bp = _jacobi(nnode, nd, tangent_bytes)
+    flops = 2 * fs + 2 * fp + 2 * 4 * ndof + 2 * 8 * ndof
     vec = 26 * ndof * 8
-    return flops, 2 * spmv + 2 * prec + vec
+    return flops, 2 * bs + 2 * bp + vec
