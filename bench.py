@@ -75,6 +75,10 @@ def parse():
     ap.add_argument("--max-resident", type=int, default=64)
     ap.add_argument("--max-krylov", type=int, default=5000,
                     help="BiCGSTAB iteration cap (profiling captures use a small cap)")
+    ap.add_argument("--serve-max-newton", type=int, default=25,
+                    help="Newton iterations per attempt in the serving comparison (both forms)")
+    ap.add_argument("--serve-max-halvings", type=int, default=2,
+                    help="increment halvings per load step in the serving comparison (both forms)")
     return ap.parse_args()
 
 
@@ -413,6 +417,7 @@ class BatchLeg:
         self.batch.enable_timers(True)
         self.batch.timers(reset=True)
         self.c0 = [s.counters() for s in self.sims]
+        self.l0 = self.batch.launches()
 
     def stop_timing(self):
         c1 = [s.counters() for s in self.sims]
@@ -424,7 +429,7 @@ class BatchLeg:
         return {"gp": gp, "newton": d("assemblies"), "krylov_iters": d("krylov_iters"), "halvings": d("halvings"),
                 "elem_integrations": sum((b["assemblies"] - a["assemblies"]) * p.mesh.nel
                                          for a, b, p in zip(self.c0, c1, self.problems)),
-                "launches": d("kernel_launches"),
+                "launches": d("kernel_launches") + self.batch.launches() - self.l0,
                 "phase_ms": {k: v[0] for k, v in tm.items()}, "phase_n": {k: v[1] for k, v in tm.items()},
                 "elements": els, "elem": self.problems[0].mesh.elem,
                 "nnode": sum(int(s.sizes.nnode) for s in self.sims), "nel": els,
@@ -647,11 +652,13 @@ def run_serving(args):
 
     clocks = Clocks(0)
     clocks.start()
-    srv = Server(budget_bytes=int(args.budget_gb * (1 << 30)), max_resident=args.max_resident, precision="fp32")
+    opts = dict(max_newton=args.serve_max_newton, max_halvings=args.serve_max_halvings)
+    srv = Server(budget_bytes=int(args.budget_gb * (1 << 30)), max_resident=args.max_resident, precision="fp32",
+                 **opts)
     js = jobs()
     rep_b = srv.run(js)
     js1 = jobs()
-    rep_1 = run_one_at_a_time(js1, precision="fp64")
+    rep_1 = run_one_at_a_time(js1, precision="fp64", **opts)
     ck = clocks.stop()
     diff = []
     for a, b in zip(sorted(js, key=lambda j: j.rid), sorted(js1, key=lambda j: j.rid)):
@@ -666,7 +673,9 @@ def run_serving(args):
                        "elements": [int(r.problem.mesh.nel) for r in trace],
                        "load_steps_per_sim": args.serve_steps, "schedule": "300 increments to the final load",
                        "arrivals": "Poisson 20/s, seed 4", "budget_gb": args.budget_gb,
-                       "max_resident": args.max_resident},
+                       "max_resident": args.max_resident, "max_newton": args.serve_max_newton,
+                       "max_halvings": args.serve_max_halvings},
+            "requests_detail": {"served_fp32": srv.records(), "one_at_a_time_fp64": [j.record() for j in js1]},
             "served_fp32_batched": rep_b, "one_at_a_time_fp64": rep_1,
             "speedup_sims_per_hour": rep_b["sims_per_hour"] / rep_1["sims_per_hour"] if rep_1["sims_per_hour"] else None,
             "curve_max_rel_diff_fp32_vs_fp64": max(diff) if diff else None,

@@ -69,8 +69,14 @@ typedef enum { LGDM_PREC_FP64 = 0, LGDM_PREC_FP32_TANGENT = 1 } lgdm_precision;
  * prolongation, Galerkin coarse matrices (fixed-order sums of the finer
  * level's node blocks, no atomics), one damped (0.7) node-block Jacobi sweep
  * before and after each coarse correction, and a dense inverse of the
- * coarsest matrix.  The multigrid set-up runs after every assembly.  The
- * GMRES fallback always uses the node blocks. */
+ * coarsest matrix.  The hierarchy is built from the secant tangent (the
+ * tangent of Eq. 11a-d with the loading indicator chi taken as 0; its
+ * diagonal blocks are positive definite), while BiCGSTAB iterates on the
+ * consistent tangent: a damaged, indefinite consistent tangent keeps a
+ * well-behaved preconditioner and Newton keeps its quadratic convergence.
+ * The assembly writes both matrices; the multigrid set-up runs after every
+ * assembly.  The GMRES fallback uses the node blocks (of the secant matrix
+ * with the multigrid). */
 typedef enum { LGDM_PRECOND_JACOBI = 0, LGDM_PRECOND_NODE_BLOCK = 1, LGDM_PRECOND_MULTIGRID = 2 } lgdm_precond;
 
 typedef enum {
@@ -272,7 +278,9 @@ lgdm_status lgdm_enable_timers(lgdm_sim *sim, int32_t on);
 lgdm_status lgdm_get_timers(lgdm_sim *sim, double *ms, int64_t *launches);
 lgdm_status lgdm_reset_timers(lgdm_sim *sim);
 
-/* Counters since creation: [0] kernel launches, [1] assemblies,
+/* Counters since creation: [0] kernel launches made for this simulation
+ * (the batched passes of a batch are counted by the batch,
+ * lgdm_batch_get_launches), [1] assemblies,
  * [2] Krylov iterations, [3] Newton iterations, [4] committed load steps,
  * [5] increment halvings, [6] Newton iterations taken with the secant
  * tangent (see lgdm_newton_step).  n entries are written (n <= 7). */
@@ -353,6 +361,10 @@ lgdm_status lgdm_batch_get_tuning(const lgdm_batch *batch, int32_t *block_thread
  * get returns the setting and the number of waves. */
 lgdm_status lgdm_batch_set_solve_tuning(lgdm_batch *batch, int32_t nodes_per_block);
 lgdm_status lgdm_batch_get_solve_tuning(const lgdm_batch *batch, int32_t *nodes_per_block, int32_t *waves);
+/* Kernels issued by the batch's own batched passes since creation (directly
+ * or as nodes of its CUDA graph).  Launches made for one member alone (its
+ * begin_step, commit, GMRES fallback) are in that member's counters. */
+lgdm_status lgdm_batch_get_launches(const lgdm_batch *batch, int64_t *launches);
 /* Autotuner: times the batched assembly for every block size and grid factor
  * with CUDA events on the current states and keeps the fastest. */
 lgdm_status lgdm_batch_autotune(lgdm_batch *batch, int32_t *block_threads, int32_t *grid_factor, double *ms);

@@ -106,6 +106,7 @@ _SIGS = {
     "lgdm_batch_get_tuning": (C.c_int, [C.c_void_p, _ip, _ip, _ip]),
     "lgdm_batch_set_solve_tuning": (C.c_int, [C.c_void_p, C.c_int32]),
     "lgdm_batch_get_solve_tuning": (C.c_int, [C.c_void_p, _ip, _ip]),
+    "lgdm_batch_get_launches": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64)]),
     "lgdm_batch_autotune": (C.c_int, [C.c_void_p, _ip, _ip, _dp]),
     "lgdm_batch_assemble": (C.c_int, [C.c_void_p, _ip]),
     "lgdm_batch_enable_timers": (C.c_int, [C.c_void_p, C.c_int32]),

@@ -64,6 +64,12 @@ class Batch:
         self._ck(self._lib.lgdm_batch_get_solve_tuning(self.h, C.byref(npb), C.byref(w)))
         return {"nodes_per_block": npb.value, "waves": w.value}
 
+    def launches(self):
+        """Kernels issued by the batched passes since creation."""
+        n = C.c_int64()
+        self._ck(self._lib.lgdm_batch_get_launches(self.h, C.byref(n)))
+        return int(n.value)
+
     def autotune(self):
         bt, gf, ms = C.c_int32(), C.c_int32(), C.c_double()
         self._ck(self._lib.lgdm_batch_autotune(self.h, C.byref(bt), C.byref(gf), C.byref(ms)))

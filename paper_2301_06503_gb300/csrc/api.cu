@@ -157,6 +157,7 @@ struct lgdm_sim {
   int32_t n_reac_elems = 0, n_reac = 0;
   double *u = nullptr, *u_commit = nullptr, *kappa_hist = nullptr;
   void *Ke = nullptr, *vals = nullptr, *minv = nullptr;
+  void *Kcor = nullptr, *vals_sec = nullptr;     // multigrid: loading-indicator terms, secant matrix
   double *re = nullptr, *rraw = nullptr, *rhs = nullptr;
   double *kv[11] = {};
   double *gm_V = nullptr, *gm_R = nullptr, *gm_y = nullptr, *gm_dots = nullptr, *gm_final = nullptr;
@@ -358,7 +359,10 @@ void carve(lgdm_sim &s, Carver &c) {
   s.d_gstart = c.take<int32_t>(2);
   const int L = s.amg_levels;
   s.h_lev.assign(L, AmgLevel{});
+  s.Kcor = s.vals_sec = nullptr;
   if (L > 0) {
+    s.Kcor = c.take<char>((size_t)s.nel * s.nen * s.nen * s.nd * s.tsize);
+    s.vals_sec = c.take<char>((size_t)s.nnz * s.tsize);
     s.d_lev = c.take<AmgLevel>(L);
     s.d_amg_prefix = c.take<int64_t>((size_t)4 * L);
     const size_t ts = s.tsize, nd = (size_t)s.nd;
@@ -392,12 +396,12 @@ void carve(lgdm_sim &s, Carver &c) {
     }
     const int64_t nc = s.amgh.lev[L - 1].nnode;
     s.amg_cinv = (nc <= AMG_COARSE_MAX) ? c.take<double>((size_t)(nd_sq(s.nd) * nc * nc)) : nullptr;
-    AmgLevel &V0 = s.h_lev[0];                 // level 0 is the system itself
+    AmgLevel &V0 = s.h_lev[0];                 // level 0: the system's pattern, secant values
     V0.nbr_ptr = s.nbr_ptr;
     V0.nbr = s.nbr;
     V0.pair_node = s.pair_node;
     V0.diag_pair = s.diag_pair;
-    V0.vals = s.vals;
+    V0.vals = s.vals_sec;
     V0.minv = s.minv;
   }
   s.ws_needed = c.off + 256;
@@ -520,6 +524,8 @@ BatchSim self_desc(lgdm_sim *s) {
   d.minv = s->minv;
   d.precond = (s->opt.precond == LGDM_PRECOND_JACOBI) ? LGDM_PRECOND_JACOBI : LGDM_PRECOND_NODE_BLOCK;
   d.amg = amg_info(s);
+  d.Kcor = s->Kcor;
+  d.vals_sec = s->vals_sec;
   return d;
 }
 
@@ -998,7 +1004,9 @@ KrylovArgs krylov_args(lgdm_sim *s) {
   a.ph = s->kv[7];
   a.sh = s->kv[8];
   a.xb = s->kv[9];
-  a.stall_iters = std::max(500, s->opt.max_krylov / 4);
+  // stop a solve that stopped improving: a multigrid-preconditioned solve
+  // converges in at most a few hundred iterations when it converges at all
+  a.stall_iters = (s->amg_levels > 0) ? std::max(100, s->opt.max_krylov / 20) : std::max(500, s->opt.max_krylov / 4);
   a.tile = krylov_tile(s->nnode);
   a.ntiles = (int32_t)krylov_ntiles(s->nnode);
   a.u = s->u;
@@ -1433,6 +1441,7 @@ struct lgdm_batch {
   int32_t *d_wave_members = nullptr;   // [n] members of all waves, wave after wave
   int32_t *d_wave_start = nullptr;     // [2n] block-group starts of all waves
   int nodes_per_block = 4096;          // solve tuning: target nodes per Krylov block
+  int64_t launches = 0;                // kernels issued by batched passes (directly or by the graph)
   std::vector<int32_t> h_wave_members, h_wave_start;
   int bt = 128, grid_factor = 2, sms = 152;
   bool graph_on = true, graph_ok = false, graph_tried = false;
@@ -1576,6 +1585,12 @@ lgdm_status build_waves(lgdm_batch *b, int nodes_per_block) {
 // The launches of one batched Newton step up to the solve (mode 0): the
 // element launches of every element-type group, then the gathers, then the
 // preconditioner set-ups.
+int64_t assembly_launches(const lgdm_batch *b) {
+  int64_t k = 0;
+  for (const auto &g : b->groups) k += 3 + 2 * (int64_t)g.amg.size() + (g.n_coarse > 0 ? 1 : 0);
+  return k;
+}
+
 lgdm_status batch_issue_assembly(lgdm_batch *b) {
   const int grid_cap = b->grid_factor * b->sms;
   LGDM_BMARK(b, 0);
@@ -1636,6 +1651,7 @@ void batch_resolve_timers(lgdm_batch *b) {
 }
 
 lgdm_status batch_issue_solve(lgdm_batch *b, int mode) {
+  b->launches += 2 * (int64_t)b->waves.size();          // reset + grouped solve per wave
   for (auto &w : b->waves) {
     if (b->fp32)
       LGDM_BCUDA(b, launch_bicgstab_grouped<float>(w.nd, b->d_kargs, w.d_members, w.d_start, b->d_active,
@@ -1657,8 +1673,10 @@ bool batch_capture(lgdm_batch *b, bool with_solve) {
     cudaGetLastError();
     return false;
   }
+  const int64_t counted = b->launches;         // capture records launches without running them
   lgdm_status st = batch_issue_assembly(b);
   if (st == LGDM_OK && with_solve) st = batch_issue_solve(b, 0);
+  b->launches = counted;
   e = cudaStreamEndCapture(b->stream, &g);
   bool ok = false;
   if (st == LGDM_OK && e == cudaSuccess && g) {
@@ -1684,10 +1702,12 @@ lgdm_status batch_assemble_and_solve(lgdm_batch *b) {
   }
   if (use_graph && b->graph_ok) {
     LGDM_BCUDA(b, cudaGraphLaunch(b->graph, b->stream));
+    b->launches += assembly_launches(b) + (b->graph_mode == 2 ? 2 * (int64_t)b->waves.size() : 0);
     if (b->graph_mode == 1) return batch_issue_solve(b, 0);
     return LGDM_OK;
   }
   ++b->direct_issues;
+  b->launches += assembly_launches(b);
   lgdm_status st = batch_issue_assembly(b);
   if (st != LGDM_OK) return st;
   return batch_issue_solve(b, 0);
@@ -1750,6 +1770,8 @@ lgdm_status lgdm_batch_create(lgdm_sim *const *sims, int32_t n, void *ws, size_t
       d.minv = s->minv;
       d.precond = (s->opt.precond == LGDM_PRECOND_JACOBI) ? LGDM_PRECOND_JACOBI : LGDM_PRECOND_NODE_BLOCK;
       d.amg = amg_info(s);
+      d.Kcor = s->Kcor;
+      d.vals_sec = s->vals_sec;
       hk[i] = krylov_args(s);
     }
     // element-type groups
@@ -1891,6 +1913,12 @@ lgdm_status lgdm_batch_set_solve_tuning(lgdm_batch *b, int32_t nodes_per_block) 
   return build_waves(b, nodes_per_block);
 }
 
+lgdm_status lgdm_batch_get_launches(const lgdm_batch *b, int64_t *launches) {
+  if (!b || !launches) return fail(nullptr, LGDM_ERR_INVALID_ARG, "NULL argument");
+  *launches = b->launches;
+  return LGDM_OK;
+}
+
 lgdm_status lgdm_batch_get_solve_tuning(const lgdm_batch *b, int32_t *nodes_per_block, int32_t *waves) {
   if (!b) return fail(nullptr, LGDM_ERR_INVALID_ARG, "NULL batch");
   if (nodes_per_block) *nodes_per_block = b->nodes_per_block;
@@ -1953,6 +1981,7 @@ lgdm_status batch_solve_pass(lgdm_batch *b, std::vector<int32_t> &kit, std::vect
   lgdm_status st = batch_assemble_and_solve(b);
   if (st != LGDM_OK) return st;
   LGDM_BCUDA(b, launch_collect_results(b->d_kargs, b->n, b->d_res, b->stream));
+  b->launches += 1;
   LGDM_BCUDA(b, cudaMemcpyAsync(b->h_res.data(), b->d_res, sizeof(SolveResult) * b->n, cudaMemcpyDeviceToHost, b->stream));
   LGDM_BCUDA(b, cudaStreamSynchronize(b->stream));
   batch_resolve_timers(b);
@@ -1960,7 +1989,6 @@ lgdm_status batch_solve_pass(lgdm_batch *b, std::vector<int32_t> &kit, std::vect
     if (!b->h_active[i]) continue;
     lgdm_sim *s = b->sims[i];
     SolveResult r = b->h_res[i];
-    s->counters[0] += 4;
     s->counters[1] += 1;
     s->counters[2] += r.iters;
     s->last = r;
@@ -2034,13 +2062,13 @@ lgdm_status lgdm_batch_newton_step(lgdm_batch *b, const int32_t *active, int32_t
   st = batch_issue_solve(b, 2);
   if (st != LGDM_OK) return st;
   LGDM_BCUDA(b, launch_collect_results(b->d_kargs, b->n, b->d_res, b->stream));
+  b->launches += 1;
   LGDM_BCUDA(b, cudaMemcpyAsync(b->h_res.data(), b->d_res, sizeof(SolveResult) * b->n, cudaMemcpyDeviceToHost, b->stream));
   LGDM_BCUDA(b, cudaStreamSynchronize(b->stream));
   for (int i = 0; i < b->n; ++i) {
     if (!b->h_active[i]) continue;
     lgdm_sim *s = b->sims[i];
     const SolveResult &r = b->h_res[i];
-    s->counters[0] += 1;
     s->last.converged = r.converged;
     for (int k = 0; k < 4; ++k) s->last.norms[k] = r.norms[k];
     s->assembled = false;
@@ -2119,7 +2147,10 @@ lgdm_status lgdm_batch_run_step(lgdm_batch *b, const double *loads, int32_t *new
 
 namespace {
 
-lgdm_status batch_assemble_only(lgdm_batch *b) { return batch_issue_assembly(b); }
+lgdm_status batch_assemble_only(lgdm_batch *b) {
+  b->launches += assembly_launches(b);
+  return batch_issue_assembly(b);
+}
 
 }  // namespace
 
@@ -2133,7 +2164,6 @@ lgdm_status lgdm_batch_assemble(lgdm_batch *b, const int32_t *active) {
   for (int i = 0; i < b->n; ++i)
     if (b->h_active[i]) {
       b->sims[i]->assembled = true;
-      b->sims[i]->counters[0] += 3;
       b->sims[i]->counters[1] += 1;
     }
   return st;

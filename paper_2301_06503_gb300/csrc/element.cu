@@ -155,7 +155,7 @@ template <int ELEM, typename TT, bool RES_ONLY, int BT = ELEM_THREADS, bool ENER
 __device__ __forceinline__ void element_tile(const MeshView &m, const MatConst &mc, const double *__restrict__ u,
                                              const double *__restrict__ kh, const int32_t *__restrict__ elem_list,
                                              int32_t n_elem, TT *__restrict__ Ke, double *__restrict__ re,
-                                             int64_t tile) {
+                                             int64_t tile, TT *__restrict__ Kcor = nullptr) {
   using L = ElemLayout<ELEM, TT, BT>;
   constexpr int DIM = L::DIM, NEN = L::NEN, NV = L::NV, ND = L::ND, NGP = L::NGP, EPB = L::EPB;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -442,6 +442,42 @@ __device__ __forceinline__ void element_tile(const MeshView &m, const MatConst &
 #pragma unroll
           for (int j = 0; j < ND; ++j) kout[i * NEN * ND + bb * ND + j] = acc[i][bb][j];
     }
+    if (Kcor) {
+      // the loading-indicator terms of the block row (the D'(kappa) chi terms
+      // of Eq. 11b and 11d, included above): the secant tangent is the
+      // consistent one minus them.  They sit in the micro-strain column of
+      // every node block: nd values per column node b.
+      TT cor[NEN][ND];
+#pragma unroll
+      for (int b = 0; b < NEN; ++b)
+#pragma unroll
+        for (int i = 0; i < ND; ++i) cor[b][i] = (TT)0;
+#pragma unroll
+      for (int q = 0; q < NGP; ++q) {
+        const TT *rt = RT0 + q * L::RT;
+        TT A[DIM], w[DIM];
+        TT ag = (TT)0;
+#pragma unroll
+        for (int i = 0; i < DIM; ++i) {
+          A[i] = rt[L::T_DN + a * DIM + i];
+          ag += A[i] * rt[L::T_GB + i];
+        }
+        BtV<DIM, TT>(A, rt + L::T_S, w);
+        const TT er = rt[L::T_R3] * ag;
+#pragma unroll
+        for (int b = 0; b < NEN; ++b) {
+          const TT Nb = (TT)shape_N<DIM>(q, b);
+#pragma unroll
+          for (int i = 0; i < DIM; ++i) cor[b][i] -= w[i] * Nb;
+          cor[b][DIM] += er * Nb;
+        }
+      }
+      TT *cout_ = Kcor + ((int64_t)slot * NEN + a) * NEN * ND;
+#pragma unroll
+      for (int b = 0; b < NEN; ++b)
+#pragma unroll
+        for (int i = 0; i < ND; ++i) cout_[b * ND + i] = cor[b][i];
+    }
   }
 }
 
@@ -494,7 +530,8 @@ template cudaError_t launch_element<float>(int, const MeshView &, const MatConst
 template <int ND, int NEN, typename TT>
 __device__ __forceinline__ void gather_pair(const PatternView &p, const TT *__restrict__ Ke,
                                             const double *__restrict__ re, TT *__restrict__ vals,
-                                            double *__restrict__ rraw, double *__restrict__ rhs, int64_t pr) {
+                                            double *__restrict__ rraw, double *__restrict__ rhs, int64_t pr,
+                                            const TT *__restrict__ Kcor = nullptr, TT *__restrict__ vsec = nullptr) {
   if (pr >= p.npairs) return;
   const int32_t a = p.pair_node[pr], b = p.nbr[pr];
   const int32_t pb = p.nbr_ptr[a];
@@ -509,6 +546,9 @@ __device__ __forceinline__ void gather_pair(const PatternView &p, const TT *__re
   double racc[ND];
 #pragma unroll
   for (int i = 0; i < ND; ++i) racc[i] = 0.0;
+  TT cacc[ND];                                   // loading-indicator terms (secant = consistent - them)
+#pragma unroll
+  for (int i = 0; i < ND; ++i) cacc[i] = (TT)0;
   const int32_t c1 = p.pc_ptr[pr + 1];
   for (int32_t c = p.pc_ptr[pr]; c < c1; ++c) {
     const int32_t pk = p.pc[c];
@@ -519,6 +559,11 @@ __device__ __forceinline__ void gather_pair(const PatternView &p, const TT *__re
     for (int i = 0; i < ND; ++i)
 #pragma unroll
       for (int j = 0; j < ND; ++j) acc[i][j] += blk[i * NEN * ND + j];
+    if (vsec) {
+      const TT *cb = Kcor + ((e * NEN + al) * NEN + bl) * ND;
+#pragma unroll
+      for (int i = 0; i < ND; ++i) cacc[i] += cb[i];
+    }
     if (diag) {
       const double *rb = re + (e * NEN + al) * ND;
 #pragma unroll
@@ -533,9 +578,11 @@ __device__ __forceinline__ void gather_pair(const PatternView &p, const TT *__re
 #pragma unroll
     for (int j = 0; j < ND; ++j) {
       const int64_t col = (int64_t)ND * b + j;
+      const bool dir = rdir || p.isdir[col];
       TT v = acc[i][j];
-      if (rdir || p.isdir[col]) v = (row == col) ? (TT)1 : (TT)0;
+      if (dir) v = (row == col) ? (TT)1 : (TT)0;
       vals[vbase + (int64_t)i * ND * deg + j] = v;
+      if (vsec) vsec[vbase + (int64_t)i * ND * deg + j] = dir ? v : (j == ND - 1 ? acc[i][j] - cacc[i] : acc[i][j]);
     }
     if (diag) {
       rraw[row] = racc[i];
@@ -814,7 +861,7 @@ batch_element_kernel(const BatchSim *__restrict__ sims, const int32_t *__restric
     if (active[sm]) {
       const BatchSim &d = sims[sm];
       element_tile<ELEM, TT, false, BT>(d.m, d.mc, d.u, d.kh, nullptr, d.m.nel, static_cast<TT *>(d.Ke), d.re,
-                                        k - tile_start[j]);
+                                        k - tile_start[j], static_cast<TT *>(d.Kcor));
     }
     __syncthreads();
   }
@@ -829,7 +876,8 @@ batch_gather_kernel(const BatchSim *__restrict__ sims, const int32_t *__restrict
   if (!active[sm]) return;
   const BatchSim &d = sims[sm];
   gather_pair<ND, NEN, TT>(d.p, static_cast<const TT *>(d.Ke), d.re, static_cast<TT *>(d.vals), d.rraw, d.rhs,
-                           (blockIdx.x - block_start[j]) * 256 + threadIdx.x);
+                           (blockIdx.x - block_start[j]) * 256 + threadIdx.x, static_cast<const TT *>(d.Kcor),
+                           static_cast<TT *>(d.vals_sec));
 }
 
 template <int ND, typename TT>
@@ -840,7 +888,9 @@ batch_precond_kernel(const BatchSim *__restrict__ sims, const int32_t *__restric
   const int sm = members[j];
   if (!active[sm]) return;
   const BatchSim &d = sims[sm];
-  precond_node<ND, TT>(d.p, static_cast<const TT *>(d.vals), d.precond, static_cast<TT *>(d.minv),
+  // with the multigrid, the smoother of the system level is built from the secant matrix
+  precond_node<ND, TT>(d.p, static_cast<const TT *>(d.vals_sec ? d.vals_sec : d.vals), d.precond,
+                       static_cast<TT *>(d.minv),
                        (int32_t)((blockIdx.x - block_start[j]) * 128 + threadIdx.x));
 }
 

@@ -181,6 +181,10 @@ struct BatchSim {
   void *minv;
   int32_t precond;
   AmgInfo amg;
+  // multigrid preconditioning of the consistent tangent by the secant one:
+  // per-element loading-indicator terms [nel][nen][nen][nd] and the secant
+  // matrix (the consistent values minus them); both NULL without multigrid
+  void *Kcor, *vals_sec;
 };
 int batch_tile_elements(int elem, int bt);
 template <typename TT>
