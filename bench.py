@@ -172,7 +172,7 @@ def traffic_for(kernel, workload):
 
 
 # the sources the profiled kernels are compiled from (host code lives in api.cu)
-KERNEL_SOURCES = ("element.cu", "krylov.cu", "lgdm_internal.cuh")
+KERNEL_SOURCES = ("element.cu", "krylov.cu", "amg.cu", "lgdm_internal.cuh", "node_block.cuh")
 
 
 def csrc_sha():
@@ -202,11 +202,20 @@ def _cores_used(cpu_s, wall_s):
     return max(1, int(round(cpu_s / wall_s))) if wall_s > 0 else 1
 
 
+# the beam's oracle sample: a slab of 4 of its 200 element columns (same
+# 1 mm hexahedra, material and notch depth), one assembly of which takes
+# seconds on a host core instead of minutes
+BEAM_SAMPLE = "a 4 x 40 x 40-hexahedra slab of the beam (same element size and material)"
+
+
 def _problem_list(workload_name, count):
-    """The problems of a workload, rebuilt from its seeded recipe (no arrays pass between processes)."""
+    """The problems of a workload's CPU sample, rebuilt from its seeded recipe
+    (no arrays pass between processes)."""
     import lgdm_inputs as li
     if workload_name == "batch":
         return li.batch_plate_problems()[:count]
+    if workload_name == "beam":
+        return [li.tpb_beam_problem(4, 40, 40, 4.0, 40.0, 40.0)]
     return workload(workload_name)[0]
 
 
@@ -250,8 +259,9 @@ def cpu_baseline(workload_name, count, label, budget_s=8.0):
     workload for about budget_s (a bounded sample)."""
     import multiprocessing as mp
     gp1, wall1, cpu1, n1 = _oracle_assembly(workload_name, count, 0, 1, budget_s)
+    what = f"{label} ({BEAM_SAMPLE})" if workload_name == "beam" else label
     one = {"value": gp1 / wall1, "unit": UNIT, "cores": _cores_used(cpu1, wall1), "kind": "oracle",
-           "sample": f"{label}: {n1} oracle assemblies (numpy element integration, scipy sparse assembly, "
+           "sample": f"{what}: {n1} oracle assemblies (numpy element integration, scipy sparse assembly, "
                      f"Dirichlet rows) at load step 1, {wall1:.1f} s wall"}
     ncores = _host_cores()
     ctx = mp.get_context("spawn")
@@ -264,7 +274,7 @@ def cpu_baseline(workload_name, count, label, budget_s=8.0):
     cpu = sum(r[2] for r in res)
     n = sum(r[3] for r in res)
     return {"value": gp / span, "unit": UNIT, "cores": _cores_used(cpu, span), "kind": "oracle",
-            "sample": f"{label}: {n} oracle assemblies at load step 1 in {ncores} spawned processes (each "
+            "sample": f"{what}: {n} oracle assemblies at load step 1 in {ncores} spawned processes (each "
                       f"assembling different problems for {budget_s:.0f} s; throughput = Gauss points / "
                       f"longest worker time {span:.1f} s; pool wall {wall:.1f} s with start-up)",
             "one_core": one}
@@ -283,6 +293,10 @@ def run_reference(args):
     if args.workload == "batch":
         probs = probs[:args.batch_count]
         label = f"batch_{len(probs)}_plates_q4_20to300"
+    sample = label
+    if args.workload == "beam":
+        probs = _problem_list("beam", 1)
+        sample = f"{label} ({BEAM_SAMPLE})"
     k = [0]
 
     def step():
@@ -315,7 +329,7 @@ def run_reference(args):
                                                   "Dirichlet rows) of the next problem at load step 1",
                        "l2": "n/a (CPU)"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": f"{label}: {args.steps} oracle assemblies, problems in order"},
+                             "sample": f"{sample}: {args.steps} oracle assemblies, problems in order"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
