@@ -27,6 +27,7 @@ class Material:
     c: float = 4.0              # gradient parameter, mm^2
     h: Optional[float] = None   # coupling modulus; None -> 1e-9 * E
     evm_variant: int = 0        # 0: de Vree coefficients, 1: literal print
+    h_stress: int = 0           # 0: stress without the h-term, 1: Eq. 2 literal (with it)
 
     def __post_init__(self):
         if self.h is None:

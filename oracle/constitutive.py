@@ -124,6 +124,43 @@ def equivalent_strain(eps, dim, nu, k, variant=0):
     return eq, d
 
 
+def equivalent_strain_hessian(eps, dim, nu, k, variant=0):
+    """Second derivative of the equivalent strain (Eq. A.3) with respect to the
+    Voigt strain (engineering shear), shape (..., nv, nv).
+
+    With Q = b2 I1^2 + cJ J2 and eps_eq = a I1 + sqrt(Q) / (2k):
+    d2 eps_eq = [d2Q / (2 sqrt Q) - dQ (x) dQ / (4 Q^(3/2))] / (2k), where
+    dQ = 2 b2 I1 dI1 + cJ dJ2 and d2Q = 2 b2 dI1 (x) dI1 + cJ d2J2; d2J2 is
+    delta_ij - 1/3 between normal components and 1/2 on each shear component
+    (J2 = 1/2 dev(eps):dev(eps), tensor shear gamma/2).  Zero where Q vanishes
+    and in 1D (eps_eq is the axial strain there).
+    """
+    eps = np.asarray(eps)
+    nv = eps.shape[-1]
+    if dim == 1:
+        return np.zeros(eps.shape + (1,), dtype=eps.dtype)
+    a, b2, cJ = evm_coefficients(nu, k, variant)
+    nn = dim                                             # normal components (plane strain: xx, yy)
+    I1 = np.sum(eps[..., :nn], axis=-1)
+    dI1 = np.zeros(nv)
+    dI1[:nn] = 1.0
+    dJ2 = np.concatenate([eps[..., :nn] - I1[..., None] / 3.0, eps[..., nn:] / 2.0], axis=-1)
+    ee = np.sum(eps[..., :nn] ** 2, axis=-1) + 0.5 * np.sum(eps[..., nn:] ** 2, axis=-1)
+    J2 = 0.5 * (ee - I1 ** 2 / 3.0)
+    Q = b2 * I1 ** 2 + cJ * J2
+    d2J2 = np.zeros((nv, nv))
+    d2J2[:nn, :nn] = np.eye(nn) - 1.0 / 3.0
+    d2J2[nn:, nn:] = 0.5 * np.eye(nv - nn)
+    dQ = 2.0 * b2 * I1[..., None] * dI1 + cJ * dJ2
+    d2Q = 2.0 * b2 * np.outer(dI1, dI1) + cJ * d2J2
+    live = np.real(Q) > 0.0
+    Qs = np.where(live, Q, 1.0)
+    root = np.sqrt(Qs)
+    H = (d2Q / (2.0 * root[..., None, None])
+         - np.einsum("...i,...j->...ij", dQ, dQ) / (4.0 * (Qs * root)[..., None, None])) / (2.0 * k)
+    return np.where(live[..., None, None], H, 0.0)
+
+
 def free_energy_density(D, eps, C_eps, h, eps_eq, ebar, g, c, grad_ebar):
     """Free energy density (Eq. 1).
 

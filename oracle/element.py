@@ -12,7 +12,11 @@ tangent (Eq. 11a-d) and of the residual (Eq. 11e-f, written as r = -F):
   K_ee  = sum_q [h N N^T + g h c B_e^T B_e + h c g' D' chi (B_e^T grad ebar) N^T] dV  (11d)
 
 Readings: sigma carries no h-term (the paper's own element code forms
-f_u = -k_uu u_e and passes no h to its K_ue routine); the gradient term of
+f_u = -k_uu u_e and passes no h to its K_ue routine) unless the material
+asks for the Eq. 2-literal stress (``h_stress`` = 1):
+sigma = (1 - D) C eps + h (eps_eq - ebar) d eps_eq/d eps, whose consistent
+tangent adds B_u^T [h d (x) d + h (eps_eq - ebar) d2 eps_eq/d eps2] B_u dV to
+K_uu and -B_u^T h d N^T dV to K_ue (Eq. 11a-b in full); the gradient term of
 F_e takes the sign that makes F_e = -r_e; dg/dkappa in Eq. 11d is
 g'(D) D'(kappa) chi.  Equal-order elements: 2-node bar, 4-node quad and
 8-node hex for both fields, with 2, 2x2, 2x2x2 Gauss points at +-1/sqrt(3).
@@ -141,6 +145,9 @@ def element_terms(mesh, mat, u, kappa_hist, elems=None):
     Ceps = np.einsum("evw,eqw->eqv", Ce, eps)
     sigma = (1.0 - D)[..., None] * Ceps
     h, c = mat.h, mat.c
+    h_stress = int(getattr(mat, "h_stress", 0))
+    if h_stress:
+        sigma = sigma + (h * (eps_eq - ebar))[..., None] * deq
 
     ru = np.einsum("eqvk,eqv,eq->ek", B, sigma, dV)
     re = (np.einsum("qa,eq->ea", N, h * (ebar - eps_eq) * dV)
@@ -148,6 +155,11 @@ def element_terms(mesh, mat, u, kappa_hist, elems=None):
 
     Kuu = np.einsum("eqvk,evw,eqwl,eq->ekl", B, Ce, B, (1.0 - D) * dV)
     Kue = -np.einsum("eqvk,eqv,qb,eq->ekb", B, Ceps, N, dD * chi * dV)
+    if h_stress:
+        Hq = cm.equivalent_strain_hessian(eps, d, mat.nu, mat.k, mat.evm_variant)
+        Mq = (np.einsum("eqv,eqw->eqvw", deq, deq) + (eps_eq - ebar)[..., None, None] * Hq) * (h * dV)[..., None, None]
+        Kuu = Kuu + np.einsum("eqvk,eqvw,eqwl->ekl", B, Mq, B)
+        Kue = Kue - np.einsum("eqvk,eqv,qb,eq->ekb", B, deq, N, h * dV)
     Keu = -np.einsum("qa,eqv,eqvk,eq->eak", N, deq, B, h * dV)
     Kee = (np.einsum("qa,qb,eq->eab", N, N, h * dV)
            + np.einsum("eqai,eqbi,eq->eab", dNdx, dNdx, g * h * c * dV)

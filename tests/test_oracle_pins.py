@@ -27,6 +27,10 @@ Each test names the pin it implements:
   P13 tangent structure: K_uu symmetric, K_ue = 0 without loading points
   P14 damaged-region volume: sum of dV over the Gauss points with D above a
       threshold equals the volume of the elements built to carry that damage
+  P15 Eq. 2-literal stress (h-term in sigma): the Hessian of Eq. A.3 equals
+      the complex-step derivative of its gradient; the full tangent equals
+      the complex-step Jacobian of the residual; the residual is then the
+      exact gradient of Eq. 1 (frozen history), the h-term included
 """
 import dataclasses
 
@@ -577,3 +581,72 @@ def test_p14_damaged_volume():
     np.testing.assert_allclose(nw.damaged_volume(p, st, 0.9), sum(area(e) for e in chosen), rtol=1e-13)
     np.testing.assert_allclose(nw.damaged_volume(p, st, 0.0), 2400.0, rtol=1e-13)
     assert nw.damaged_volume(p, st, 0.999999) == 0.0
+
+
+# ---------------------------------------------------------------- P15
+@pytest.mark.parametrize("dim,variant", [(2, 0), (3, 0), (3, 1)])
+def test_p15_equivalent_strain_hessian(dim, variant):
+    rng = np.random.default_rng(7 + dim + variant)
+    nv = 3 if dim == 2 else 6
+    for _ in range(5):
+        v = rng.normal(size=nv) * 1e-4
+        H = cm.equivalent_strain_hessian(v, dim, 0.2, 10.0, variant)
+        hs = 1e-30
+        for j in range(nv):
+            vc = v.astype(complex)
+            vc[j] += 1j * hs
+            _, dc = cm.equivalent_strain(vc, dim, 0.2, 10.0, variant)
+            assert np.abs(dc.imag / hs - H[:, j]).max() <= 1e-9 * np.abs(H).max()
+        assert np.abs(H - H.T).max() <= 1e-12 * np.abs(H).max()
+
+
+def _h_material(dim):
+    base = MAT if dim > 1 else li.Material(nu=0.0, k=1.0)
+    return dataclasses.replace(base, h=0.05 * base.E, h_stress=1)
+
+
+@pytest.mark.parametrize("mi", [0, 1, 2])
+def test_p15_literal_stress_tangent_is_complex_step_jacobian(mi):
+    mesh = list(_small_meshes())[mi]
+    mat = _h_material(mesh.dim)
+    u, kh = li.random_state(mesh, seed=60 + mi, kappa0=mat.kappa0)
+    K, r = asm.assemble(mesh, mat, u, kh)
+    K = K.toarray()
+    hs = 1e-30
+    J = np.empty_like(K)
+    for j in range(mesh.ndof):
+        uc = u.astype(complex)
+        uc[j] += 1j * hs
+        _, rc = asm.assemble(mesh, mat, uc, kh, with_tangent=False)
+        J[:, j] = rc.imag / hs
+    bk, bj = _blocks(mesh, K), _blocks(mesh, J)
+    for name in bk:
+        scale = np.abs(bj[name]).max()
+        assert scale > 0.0
+        assert np.abs(bk[name] - bj[name]).max() <= 1e-10 * scale, name
+    # the variant changes the displacement blocks and the residual
+    K0, r0 = asm.assemble(mesh, dataclasses.replace(mat, h_stress=0), u, kh)
+    b0 = _blocks(mesh, K0.toarray())
+    assert np.abs(b0["uu"] - bk["uu"]).max() > 1e-3 * np.abs(bk["uu"]).max()
+    assert np.abs(r0 - r).max() > 1e-3 * np.abs(r).max()
+
+
+@pytest.mark.parametrize("mi", [1, 2])
+def test_p15_literal_stress_residual_is_energy_gradient(mi):
+    """With the h-term in the stress, the coupled residual is the exact
+    gradient of Eq. 1 at a frozen history (no loading point): d Psi / d u =
+    r_u and d Psi / d ebar = r_e, with h far from negligible."""
+    mesh = list(_small_meshes())[mi]
+    mat = _h_material(mesh.dim)
+    u, kh = li.random_state(mesh, seed=70 + mi, kappa0=mat.kappa0)
+    ebar = el.gp_ebar(mesh, u).ravel()
+    kh = np.maximum(kh, ebar + 0.1 * mat.kappa0)
+    prob = li.Problem("p15", mesh, mat, li.BCs(np.zeros(0, np.int32), np.zeros(0)), 1.0, 1)
+    _, r = asm.assemble(mesh, mat, u, kh, with_tangent=False)
+    hs = 1e-30
+    grad = np.empty(mesh.ndof)
+    for j in range(mesh.ndof):
+        uc = u.astype(complex)
+        uc[j] += 1j * hs
+        grad[j] = nw.free_energy(prob, nw.State(uc, kh)).imag / hs
+    assert np.abs(grad - r).max() <= 1e-10 * np.abs(r).max()
