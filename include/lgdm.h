@@ -104,10 +104,15 @@ typedef struct {
 /* Material (Sec. 2.1, Appendix A).  eta is the exponent "n" of Eq. A.4.
  * evm_variant 0 uses 12k/(1+nu)^2 in front of J2 = dev(eps):dev(eps)/2 in
  * Eq. A.3 (uniaxial stress gives eps_eq = axial strain); 1 uses the printed
- * 2k/(1-nu)^2.  In 1D eps_eq is the axial strain and nu, k are ignored. */
+ * 2k/(1-nu)^2.  In 1D eps_eq is the axial strain and nu, k are ignored.
+ * h_stress 0: sigma = (1 - D) C eps (the paper's element code); 1: Eq. 2 as
+ * printed, sigma = (1 - D) C eps + h (eps_eq - ebar) d eps_eq/d eps, with the
+ * full consistent tangent (K_uu gains B^T [h d (x) d + h (eps_eq - ebar)
+ * d2 eps_eq/d eps2] B dV, K_ue gains -B^T h d N^T dV; Eq. 11a-b). */
 typedef struct {
   double E, nu, k, kappa0, alpha, beta, R, eta, c, h;
   int32_t evm_variant;
+  int32_t h_stress;
 } lgdm_material;
 
 /* Displacement control: u[dir_dof[i]] = dir_scale[i] * load at each load

@@ -36,7 +36,7 @@ class Mesh(C.Structure):
 
 class Material(C.Structure):
     _fields_ = [(n, C.c_double) for n in ("E", "nu", "k", "kappa0", "alpha", "beta", "R", "eta", "c", "h")] + \
-               [("evm_variant", C.c_int32)]
+               [("evm_variant", C.c_int32), ("h_stress", C.c_int32)]
 
 
 class BCs(C.Structure):

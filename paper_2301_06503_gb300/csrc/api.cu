@@ -911,7 +911,8 @@ lgdm_status lgdm_assemble(lgdm_sim *s) {
   if (s->opt.precision == LGDM_PREC_FP32_TANGENT) {
     {
       PhaseTimer pt(s, 0);
-      LGDM_CUDA(s, launch_batch_element<float>(s->elem, 128, s->d_self, mem, tiles, 1, s->self_tiles, act, grid, s->stream));
+      LGDM_CUDA(s, launch_batch_element<float>(s->elem, 128, s->mc.hterm != 0, s->d_self, mem, tiles, 1, s->self_tiles,
+                                               act, grid, s->stream));
     }
     {
       PhaseTimer pt(s, 1);
@@ -925,7 +926,8 @@ lgdm_status lgdm_assemble(lgdm_sim *s) {
   } else {
     {
       PhaseTimer pt(s, 0);
-      LGDM_CUDA(s, launch_batch_element<double>(s->elem, 128, s->d_self, mem, tiles, 1, s->self_tiles, act, grid, s->stream));
+      LGDM_CUDA(s, launch_batch_element<double>(s->elem, 128, s->mc.hterm != 0, s->d_self, mem, tiles, 1, s->self_tiles,
+                                                act, grid, s->stream));
     }
     {
       PhaseTimer pt(s, 1);
@@ -1420,8 +1422,9 @@ struct lgdm_batch {
     int64_t *d_pb = nullptr, *d_nb = nullptr;
     int64_t tot_pb = 0, tot_nb = 0;
   };
-  struct Group {                       // members of one element type
+  struct Group {                       // members of one element type and stress variant
     int elem = 0, nd = 0;
+    bool hterm = false;
     std::vector<int32_t> members;
     int32_t *d_members = nullptr;
     int64_t *d_tile = nullptr, *d_gblock = nullptr, *d_pblock = nullptr;
@@ -1473,8 +1476,8 @@ namespace {
 
 size_t batch_bytes(int n) {
   // descriptors, flags, results and prefix arrays; a generous bound per member
-  const size_t amg = (size_t)3 * AMG_MAX_LEVELS * ((size_t)n * 4 + 2 * (size_t)(n + 1) * 8 + 3 * 256) +
-                     (size_t)3 * ((size_t)n * 4 + 256);
+  const size_t amg = (size_t)6 * AMG_MAX_LEVELS * ((size_t)n * 4 + 2 * (size_t)(n + 1) * 8 + 3 * 256) +
+                     (size_t)6 * ((size_t)n * 4 + 256);
   return (size_t)n * (sizeof(BatchSim) + sizeof(KrylovArgs) + sizeof(SolveResult) + 4 * 64 + 10 * 8) +
          (size_t)(n + 8) * 8 * 24 + amg + (1 << 16);
 }
@@ -1597,10 +1600,10 @@ lgdm_status batch_issue_assembly(lgdm_batch *b) {
   for (auto &g : b->groups) {
     const int grid = (int)std::min<int64_t>(g.tiles, grid_cap);
     if (b->fp32)
-      LGDM_BCUDA(b, launch_batch_element<float>(g.elem, b->bt, b->d_sims, g.d_members, g.d_tile, (int)g.members.size(),
+      LGDM_BCUDA(b, launch_batch_element<float>(g.elem, b->bt, g.hterm, b->d_sims, g.d_members, g.d_tile, (int)g.members.size(),
                                                 g.tiles, b->d_active, grid, b->stream));
     else
-      LGDM_BCUDA(b, launch_batch_element<double>(g.elem, b->bt, b->d_sims, g.d_members, g.d_tile, (int)g.members.size(),
+      LGDM_BCUDA(b, launch_batch_element<double>(g.elem, b->bt, g.hterm, b->d_sims, g.d_members, g.d_tile, (int)g.members.size(),
                                                  g.tiles, b->d_active, grid, b->stream));
   }
   LGDM_BMARK(b, 1);
@@ -1774,15 +1777,17 @@ lgdm_status lgdm_batch_create(lgdm_sim *const *sims, int32_t n, void *ws, size_t
       d.vals_sec = s->vals_sec;
       hk[i] = krylov_args(s);
     }
-    // element-type groups
-    for (int elem : {LGDM_L2, LGDM_Q4, LGDM_H8}) {
-      lgdm_batch::Group g;
-      g.elem = elem;
-      g.nd = dim_of(elem) + 1;
-      for (int i = 0; i < n; ++i)
-        if (b->sims[i]->elem == elem) g.members.push_back(i);
-      if (!g.members.empty()) b->groups.push_back(g);
-    }
+    // groups of one element type and stress variant (one element kernel each)
+    for (int elem : {LGDM_L2, LGDM_Q4, LGDM_H8})
+      for (int ht = 0; ht < 2; ++ht) {
+        lgdm_batch::Group g;
+        g.elem = elem;
+        g.nd = dim_of(elem) + 1;
+        g.hterm = ht != 0;
+        for (int i = 0; i < n; ++i)
+          if (b->sims[i]->elem == elem && (b->sims[i]->mc.hterm != 0) == g.hterm) g.members.push_back(i);
+        if (!g.members.empty()) b->groups.push_back(g);
+      }
     const int epb = 1;   // prefixes are in tiles of the tuned block size: rebuilt by set_tiles
     (void)epb;
     const size_t nm_max = n;

@@ -49,6 +49,7 @@ MatConst make_matconst(const lgdm_material &m, int dim) {
   c.h = m.h;
   c.c = m.c;
   c.secant = 0;
+  c.hterm = m.h_stress ? 1 : 0;
   return c;
 }
 
@@ -129,17 +130,19 @@ __device__ __forceinline__ double equivalent_strain(const MatConst &mc, const do
 // ------------------------------------------------------------------ element kernel
 constexpr int ELEM_THREADS = 128;
 
-template <int ELEM, typename TT, int BT = ELEM_THREADS>
+template <int ELEM, typename TT, int BT = ELEM_THREADS, bool HT = false>
 struct ElemLayout {
   static constexpr int DIM = Elem<ELEM>::DIM, NEN = Elem<ELEM>::NEN, NV = Elem<ELEM>::NV;
   static constexpr int ND = DIM + 1, NGP = NEN, EPB = BT / NEN;
   // double record per Gauss point: dNdx[NEN][DIM], sig dV[NV], rho2, rho4, gbar[DIM]
   static constexpr int RD = NEN * DIM + NV + 2 + DIM;
   static constexpr int O_DN = 0, O_SIG = NEN * DIM, O_R2 = O_SIG + NV, O_R4 = O_R2 + 1, O_GB = O_R4 + 1;
-  // tangent record per Gauss point (TT): dNdx[NEN][DIM], z[NEN][DIM], lam', mu', s[NV], rho1, rho2, rho3, gbar[DIM]
-  static constexpr int RT = 2 * NEN * DIM + 2 + NV + 3 + DIM;
+  // tangent record per Gauss point (TT): dNdx[NEN][DIM], z[NEN][DIM], lam', mu', s[NV], rho1, rho2, rho3,
+  // gbar[DIM]; with the h-term stress also q[NEN][DIM] and the coefficients cy, cq of its rank-one terms
+  static constexpr int RT = 2 * NEN * DIM + 2 + NV + 3 + DIM + (HT ? NEN * DIM + 2 : 0);
   static constexpr int T_DN = 0, T_Z = NEN * DIM, T_LAM = 2 * NEN * DIM, T_MU = T_LAM + 1, T_S = T_MU + 1,
                        T_R1 = T_S + NV, T_R2 = T_R1 + 1, T_R3 = T_R2 + 1, T_GB = T_R3 + 1;
+  static constexpr int T_Q = T_GB + DIM, T_CY = T_Q + NEN * DIM, T_CQ = T_CY + 1;
   static constexpr int RDS = (NGP * RD) | 1;                // odd stride: fewer bank conflicts
   static constexpr int RTS = (NGP * RT) | 1;
   static constexpr size_t BYTES_D = sizeof(double) *
@@ -151,12 +154,12 @@ struct ElemLayout {
 
 // One tile of EPB elements: phase 1 and phase 2 for tile `tile` of an
 // element list.  Every thread of the block calls it (it synchronises).
-template <int ELEM, typename TT, bool RES_ONLY, int BT = ELEM_THREADS, bool ENERGY = false>
+template <int ELEM, typename TT, bool RES_ONLY, int BT = ELEM_THREADS, bool ENERGY = false, bool HT = false>
 __device__ __forceinline__ void element_tile(const MeshView &m, const MatConst &mc, const double *__restrict__ u,
                                              const double *__restrict__ kh, const int32_t *__restrict__ elem_list,
                                              int32_t n_elem, TT *__restrict__ Ke, double *__restrict__ re,
                                              int64_t tile, TT *__restrict__ Kcor = nullptr) {
-  using L = ElemLayout<ELEM, TT, BT>;
+  using L = ElemLayout<ELEM, TT, BT, HT>;
   constexpr int DIM = L::DIM, NEN = L::NEN, NV = L::NV, ND = L::ND, NGP = L::NGP, EPB = L::EPB;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double *sN = reinterpret_cast<double *>(smem_raw);            // [NGP][NEN]
@@ -302,9 +305,10 @@ __device__ __forceinline__ void element_tile(const MeshView &m, const MatConst &
     for (int b = 0; b < NEN; ++b)
 #pragma unroll
       for (int i = 0; i < DIM; ++i) rd[L::O_DN + b * DIM + i] = g[b][i];
-#pragma unroll
-    for (int v = 0; v < NV; ++v) rd[L::O_SIG + v] = omD * dV * ce[v];
     const double hdV = mc.h * dV;
+#pragma unroll
+    for (int v = 0; v < NV; ++v)   // Eq. 2 literal: sigma also carries h (eps_eq - ebar) d eps_eq/d eps
+      rd[L::O_SIG + v] = omD * dV * ce[v] + (HT ? hdV * (eq - eb) * deq[v] : 0.0);
     rd[L::O_R2] = gi * mc.h * mc.c * dV;
     rd[L::O_R4] = hdV * (eb - eq);
 #pragma unroll
@@ -334,6 +338,47 @@ __device__ __forceinline__ void element_tile(const MeshView &m, const MatConst &
       rt[L::T_R3] = (TT)(mc.h * mc.c * dgi * lin);
 #pragma unroll
       for (int i = 0; i < DIM; ++i) rt[L::T_GB + i] = (TT)gb[i];
+      if constexpr (HT) {
+        // tangent of the h-term stress: h dV [d (x) d + psi d2 eps_eq], psi = eps_eq - ebar.
+        // With Q = b2 I1^2 + cJ J2, d2 eps_eq = [d2Q / (2 sqrt Q) - dQ (x) dQ / (4 Q^1.5)] / (2k),
+        // d2Q = 2 b2 dI1 (x) dI1 + cJ d2J2, and B_a^T d2J2 B_b = -a_i b_j / 3 + (a_j b_i + a.b delta_ij) / 2:
+        // the isotropic parts join lam', mu'; d (x) d and dQ (x) dQ are rank-one (z and q vectors).
+        const double hdVp = hdV * (eq - eb);
+        double lx = 0.0, mx = 0.0, c3 = 0.0, vq[NV];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) vq[v] = 0.0;
+        if constexpr (DIM > 1) {
+          double I1 = 0.0, ee = 0.0;
+#pragma unroll
+          for (int i = 0; i < DIM; ++i) { I1 += eps[i]; ee += eps[i] * eps[i]; }
+#pragma unroll
+          for (int v = DIM; v < NV; ++v) ee += 0.5 * eps[v] * eps[v];
+          const double Q = mc.evm_b2 * I1 * I1 + mc.evm_cJ * 0.5 * (ee - I1 * I1 * (1.0 / 3.0));
+          if (Q > 0.0) {
+            const double root = sqrt(Q);
+            const double c1 = hdVp * mc.inv2k * mc.evm_b2 / root;
+            const double c2 = hdVp * mc.inv2k * mc.evm_cJ / (2.0 * root);
+            c3 = hdVp * mc.inv2k / (4.0 * Q * root);
+            lx = c1 - c2 * (1.0 / 3.0);
+            mx = 0.5 * c2;
+#pragma unroll
+            for (int i = 0; i < DIM; ++i) vq[i] = 2.0 * mc.evm_b2 * I1 + mc.evm_cJ * (eps[i] - I1 * (1.0 / 3.0));
+#pragma unroll
+            for (int v = DIM; v < NV; ++v) vq[v] = mc.evm_cJ * 0.5 * eps[v];
+          }
+        }
+        rt[L::T_LAM] = (TT)(omD * es * mc.lam * dV + lx);
+        rt[L::T_MU] = (TT)(omD * es * mc.mu * dV + mx);
+#pragma unroll
+        for (int b = 0; b < NEN; ++b) {
+          double qb[DIM];
+          BtV<DIM, double>(g[b], vq, qb);
+#pragma unroll
+          for (int i = 0; i < DIM; ++i) rt[L::T_Q + b * DIM + i] = (TT)qb[i];
+        }
+        rt[L::T_CY] = (TT)(hdV > 0.0 ? 1.0 / hdV : 0.0);   // h dV (B^T d)(B^T d)^T = z z^T / (h dV)
+        rt[L::T_CQ] = (TT)(-c3);
+      }
     }
   }
   __syncthreads();
@@ -397,6 +442,17 @@ __device__ __forceinline__ void element_tile(const MeshView &m, const MatConst &
         BtV<DIM, TT>(A, rt + L::T_S, w);               // B_a^T (C eps) D' chi dV
         const TT ea = Na * rt[L::T_R1] + rt[L::T_R3] * ag;
         const TT nNa = -Na;
+        TT cza[DIM], cqa[DIM];                         // h-term stress: rank-one factors of row node a
+        if constexpr (HT) {
+          const TT cy = rt[L::T_CY], cq = rt[L::T_CQ];
+#pragma unroll
+          for (int i = 0; i < DIM; ++i) {
+            const TT za = rt[L::T_Z + a * DIM + i];
+            w[i] += za;                                // K_ue gains -B_a^T h d N_b dV
+            cza[i] = cy * za;
+            cqa[i] = cq * rt[L::T_Q + a * DIM + i];
+          }
+        }
 #pragma unroll
         for (int bb = 0; bb < BC; ++bb) {
           const int b = b0 + bb;
@@ -421,6 +477,12 @@ __device__ __forceinline__ void element_tile(const MeshView &m, const MatConst &
                 acc[i][bb][j] += la[i] * Bv[j] + ma[j] * Bv[i];
               }
             }
+          if constexpr (HT) {
+#pragma unroll
+            for (int i = 0; i < DIM; ++i)
+#pragma unroll
+              for (int j = 0; j < DIM; ++j) acc[i][bb][j] += cza[i] * Z[j] + cqa[i] * rt[L::T_Q + b * DIM + j];
+          }
           // K_ue (Eq. 11b) and K_eu (Eq. 11c)
 #pragma unroll
           for (int i = 0; i < DIM; ++i) {
@@ -481,22 +543,22 @@ __device__ __forceinline__ void element_tile(const MeshView &m, const MatConst &
   }
 }
 
-template <int ELEM, typename TT, bool RES_ONLY>
+template <int ELEM, typename TT, bool RES_ONLY, bool HT>
 __global__ void __launch_bounds__(ELEM_THREADS)
 element_kernel(MeshView m, MatConst mc, const double *__restrict__ u, const double *__restrict__ kh,
                const int32_t *__restrict__ elem_list, int32_t n_elem, TT *__restrict__ Ke,
                double *__restrict__ re) {
-  element_tile<ELEM, TT, RES_ONLY>(m, mc, u, kh, elem_list, n_elem, Ke, re, blockIdx.x);
+  element_tile<ELEM, TT, RES_ONLY, ELEM_THREADS, false, HT>(m, mc, u, kh, elem_list, n_elem, Ke, re, blockIdx.x);
 }
 
-template <int ELEM, typename TT, bool RES_ONLY>
+template <int ELEM, typename TT, bool RES_ONLY, bool HT>
 static cudaError_t launch_element_t(const MeshView &m, const MatConst &mc, const double *u,
                                     const double *kh, const int32_t *list, int32_t n, TT *Ke, double *re,
                                     cudaStream_t s) {
-  using L = ElemLayout<ELEM, TT>;
+  using L = ElemLayout<ELEM, TT, ELEM_THREADS, HT>;
   if (n <= 0) return cudaSuccess;
   const size_t smem = L::bytes(RES_ONLY);
-  auto fn = element_kernel<ELEM, TT, RES_ONLY>;
+  auto fn = element_kernel<ELEM, TT, RES_ONLY, HT>;
   cudaError_t err = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
   const int grid = (n + L::EPB - 1) / L::EPB;
@@ -508,9 +570,12 @@ template <typename TT>
 cudaError_t launch_element(int elem, const MeshView &m, const MatConst &mc, const double *u,
                            const double *kh, const int32_t *list, int32_t n, TT *Ke, double *re,
                            bool res_only, cudaStream_t s) {
-#define LGDM_EL(E)                                                                          \
-  return res_only ? launch_element_t<E, TT, true>(m, mc, u, kh, list, n, Ke, re, s)         \
-                  : launch_element_t<E, TT, false>(m, mc, u, kh, list, n, Ke, re, s)
+#define LGDM_EL(E)                                                                                          \
+  if (mc.hterm)                                                                                             \
+    return res_only ? launch_element_t<E, TT, true, true>(m, mc, u, kh, list, n, Ke, re, s)                 \
+                    : launch_element_t<E, TT, false, true>(m, mc, u, kh, list, n, Ke, re, s);               \
+  return res_only ? launch_element_t<E, TT, true, false>(m, mc, u, kh, list, n, Ke, re, s)                  \
+                  : launch_element_t<E, TT, false, false>(m, mc, u, kh, list, n, Ke, re, s)
   switch (elem) {
     case LGDM_L2: LGDM_EL(LGDM_L2);
     case LGDM_Q4: LGDM_EL(LGDM_Q4);
@@ -851,7 +916,7 @@ cudaError_t launch_damaged_volume(int elem, const MeshView &m, const MatConst &m
 
 // ------------------------------------------------------------------ batched kernels
 // Persistent: a grid of a few blocks per SM walks all members' tiles.
-template <int ELEM, typename TT, int BT>
+template <int ELEM, typename TT, int BT, bool HT>
 __global__ void __launch_bounds__(BT)
 batch_element_kernel(const BatchSim *__restrict__ sims, const int32_t *__restrict__ members,
                      const int64_t *__restrict__ tile_start, int nm, int64_t total, const int32_t *__restrict__ active) {
@@ -860,8 +925,8 @@ batch_element_kernel(const BatchSim *__restrict__ sims, const int32_t *__restric
     const int sm = members[j];
     if (active[sm]) {
       const BatchSim &d = sims[sm];
-      element_tile<ELEM, TT, false, BT>(d.m, d.mc, d.u, d.kh, nullptr, d.m.nel, static_cast<TT *>(d.Ke), d.re,
-                                        k - tile_start[j], static_cast<TT *>(d.Kcor));
+      element_tile<ELEM, TT, false, BT, false, HT>(d.m, d.mc, d.u, d.kh, nullptr, d.m.nel, static_cast<TT *>(d.Ke),
+                                                   d.re, k - tile_start[j], static_cast<TT *>(d.Kcor));
     }
     __syncthreads();
   }
@@ -894,12 +959,12 @@ batch_precond_kernel(const BatchSim *__restrict__ sims, const int32_t *__restric
                        (int32_t)((blockIdx.x - block_start[j]) * 128 + threadIdx.x));
 }
 
-template <int ELEM, typename TT, int BT>
+template <int ELEM, typename TT, int BT, bool HT>
 static cudaError_t launch_batch_element_t(const BatchSim *sims, const int32_t *members, const int64_t *tile_start,
                                           int nm, int64_t total, const int32_t *active, int grid, cudaStream_t s) {
-  using L = ElemLayout<ELEM, TT, BT>;
+  using L = ElemLayout<ELEM, TT, BT, HT>;
   const size_t smem = L::bytes(false);
-  auto fn = batch_element_kernel<ELEM, TT, BT>;
+  auto fn = batch_element_kernel<ELEM, TT, BT, HT>;
   cudaError_t err = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
   fn<<<grid, BT, smem, s>>>(sims, members, tile_start, nm, total, active);
@@ -909,29 +974,36 @@ static cudaError_t launch_batch_element_t(const BatchSim *sims, const int32_t *m
 int batch_tile_elements(int elem, int bt) { return bt / ((elem == LGDM_L2) ? 2 : (elem == LGDM_Q4) ? 4 : 8); }
 
 template <typename TT>
-cudaError_t launch_batch_element(int elem, int bt, const BatchSim *sims, const int32_t *members,
+cudaError_t launch_batch_element(int elem, int bt, bool hterm, const BatchSim *sims, const int32_t *members,
                                  const int64_t *tile_start, int nm, int64_t total, const int32_t *active, int grid,
                                  cudaStream_t s) {
   if (total <= 0) return cudaSuccess;
-#define LGDM_BE(E)                                                                                         \
-  switch (bt) {                                                                                            \
-    case 64: return launch_batch_element_t<E, TT, 64>(sims, members, tile_start, nm, total, active, grid, s);   \
-    case 128: return launch_batch_element_t<E, TT, 128>(sims, members, tile_start, nm, total, active, grid, s); \
-    case 256: return launch_batch_element_t<E, TT, 256>(sims, members, tile_start, nm, total, active, grid, s); \
-  }                                                                                                        \
+#define LGDM_BE2(E, H)                                                                                            \
+  switch (bt) {                                                                                                   \
+    case 64: return launch_batch_element_t<E, TT, 64, H>(sims, members, tile_start, nm, total, active, grid, s);   \
+    case 128: return launch_batch_element_t<E, TT, 128, H>(sims, members, tile_start, nm, total, active, grid, s); \
+    case 256: return launch_batch_element_t<E, TT, 256, H>(sims, members, tile_start, nm, total, active, grid, s); \
+  }                                                                                                               \
   return cudaErrorInvalidValue
+#define LGDM_BE(E)          \
+  if (hterm) {              \
+    LGDM_BE2(E, true);      \
+  } else {                  \
+    LGDM_BE2(E, false);     \
+  }
   switch (elem) {
     case LGDM_L2: LGDM_BE(LGDM_L2);
     case LGDM_Q4: LGDM_BE(LGDM_Q4);
     case LGDM_H8: LGDM_BE(LGDM_H8);
   }
 #undef LGDM_BE
+#undef LGDM_BE2
   return cudaErrorInvalidValue;
 }
-template cudaError_t launch_batch_element<double>(int, int, const BatchSim *, const int32_t *, const int64_t *, int,
-                                                  int64_t, const int32_t *, int, cudaStream_t);
-template cudaError_t launch_batch_element<float>(int, int, const BatchSim *, const int32_t *, const int64_t *, int,
-                                                 int64_t, const int32_t *, int, cudaStream_t);
+template cudaError_t launch_batch_element<double>(int, int, bool, const BatchSim *, const int32_t *, const int64_t *,
+                                                  int, int64_t, const int32_t *, int, cudaStream_t);
+template cudaError_t launch_batch_element<float>(int, int, bool, const BatchSim *, const int32_t *, const int64_t *,
+                                                 int, int64_t, const int32_t *, int, cudaStream_t);
 
 template <typename TT>
 cudaError_t launch_batch_gather(int elem, const BatchSim *sims, const int32_t *members, const int64_t *block_start,

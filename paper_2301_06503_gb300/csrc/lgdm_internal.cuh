@@ -50,6 +50,7 @@ struct MatConst {
   // and 11d is taken as 0, which drops the D'(kappa) terms; the residual
   // and the damage are unchanged
   int32_t secant;
+  int32_t hterm;                         // 1: Eq. 2-literal stress (h-term in sigma)
 };
 
 MatConst make_matconst(const lgdm_material &m, int dim);
@@ -94,7 +95,7 @@ struct SolveResult {
 template <typename TT>
 cudaError_t launch_element(int elem, const MeshView &m, const MatConst &mc, const double *u,
                            const double *kappa_hist, const int32_t *elem_list, int32_t n_elem,
-                           TT *Ke, double *re, bool residual_only, cudaStream_t s);
+                           TT *Ke, double *re, bool residual_only, cudaStream_t s);   // mc.hterm selects the variant
 template <typename TT>
 cudaError_t launch_gather(int elem, const PatternView &p, const TT *Ke, const double *re,
                           TT *vals, double *rraw, double *rhs, cudaStream_t s);
@@ -188,7 +189,7 @@ struct BatchSim {
 };
 int batch_tile_elements(int elem, int bt);
 template <typename TT>
-cudaError_t launch_batch_element(int elem, int bt, const BatchSim *sims, const int32_t *members,
+cudaError_t launch_batch_element(int elem, int bt, bool hterm, const BatchSim *sims, const int32_t *members,
                                  const int64_t *tile_start, int nm, int64_t total, const int32_t *active, int grid,
                                  cudaStream_t s);
 template <typename TT>

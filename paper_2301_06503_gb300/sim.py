@@ -84,7 +84,7 @@ class Sim:
         m = _MeshArgs(mesh)
         mat = L.Material(*[float(getattr(material, n)) for n in
                            ("E", "nu", "k", "kappa0", "alpha", "beta", "R", "eta", "c", "h")],
-                         int(getattr(material, "evm_variant", 0)))
+                         int(getattr(material, "evm_variant", 0)), int(getattr(material, "h_stress", 0)))
         dof, scale = _i32(bcs.dir_dof), _f64(bcs.dir_scale)
         b = L.BCs(int(dof.shape[0]), _p(dof, C.c_int32), _p(scale, C.c_double))
         self.options = make_options(**opts)

@@ -75,6 +75,34 @@ def test_fp64_assembly_literal_equivalent_strain_coefficients(name):
     s.close()
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("name", ["bar", "plate", "beam"])
+def test_literal_h_stress_assembly_matches_oracle(name, precision):
+    """Eq. 2-literal stress (h-term in sigma) with its full consistent tangent
+    (h d (x) d and h (eps_eq - ebar) times the Hessian of Eq. A.3 in K_uu, -h d
+    N^T in K_ue), h = 0.05 E so that these terms are large: FP64 to 1e-12, the
+    FP32 tangent to float accuracy; the residual stays FP64."""
+    import dataclasses
+    p = _problems()[name]
+    mat = dataclasses.replace(p.material, h=0.05 * p.material.E, h_stress=1)
+    p = dataclasses.replace(p, material=mat)
+    u, kh = li.random_state(p.mesh, seed=19, kappa0=mat.kappa0)
+    s = _sim(p, precision=precision)
+    s.set_state(u, kh)
+    s.assemble()
+    K, rhs = gpu_csr(s)
+    Kref, rref, rraw = oracle_system(p.mesh, mat, p.bcs, u, kh)
+    K0, _, r0 = oracle_system(p.mesh, dataclasses.replace(mat, h_stress=0), p.bcs, u, kh)
+    assert max(block_errors(p.mesh, K0, Kref).values()) > 1e-3          # the variant matters here
+    eb = block_errors(p.mesh, K, Kref)
+    ev = vector_errors(p.mesh, rhs, rref)
+    assert max(eb.values()) <= (1e-12 if precision == "fp64" else 2e-6), eb
+    assert max(ev.values()) <= 1e-12, ev
+    ev = vector_errors(p.mesh, s.field("residual"), rraw)
+    assert max(ev.values()) <= 1e-12, ev
+    s.close()
+
+
 @pytest.mark.parametrize("name", ["plate", "beam"])
 def test_fp32_tangent_assembly(name):
     p = _problems()[name]

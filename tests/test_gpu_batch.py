@@ -101,3 +101,28 @@ def test_batch_fp32_tangent_members():
     for j, p in enumerate(probs):
         r1, *_ = _alone(p, 4, precision="fp32")
         assert got[j] == r1[-1]
+
+
+def test_batch_mixing_stress_variants_equals_alone():
+    """A batch whose members use both stress forms (one element kernel per
+    element type and variant): every member bitwise equal to itself alone."""
+    import dataclasses
+    from paper_2301_06503_gb300 import Batch, Sim
+    probs = _problems()[:3]
+    probs[1] = dataclasses.replace(probs[1], material=dataclasses.replace(probs[1].material, h=1e-3 * 20000.0,
+                                                                          h_stress=1))
+    stream = torch.cuda.Stream()
+    sims = [Sim(p.mesh, p.material, p.bcs, stream=stream) for p in probs]
+    b = Batch(sims)
+    steps = 4
+    reac = np.zeros((steps, len(probs)))
+    for n in range(1, steps + 1):
+        its, st = b.run_step([p.load(n) for p in probs])
+        assert np.all(st == 0)
+        reac[n - 1] = [s.reaction() for s in sims]
+    b.close()
+    for s in sims:
+        s.close()
+    for j, p in enumerate(probs):
+        r1, _, _, _ = _alone(p, steps)
+        assert np.array_equal(reac[:, j], r1), j

@@ -161,6 +161,22 @@ def test_beam_reduced_curve():
     _curve_check(p, 30)
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_literal_h_stress_plate_curve(precision):
+    """Eq. 2-literal stress on a 16 x 16 notched plate with h = 1e-3 E (large
+    enough for the h-term to move the curve by about 1 %), 16 load steps of a
+    240-step schedule (damaging, no halving): the curve matches the oracle's
+    run of the same variant."""
+    import dataclasses
+    base = li.sen_plate_problem(16, 16, n_steps=240)
+    mat = dataclasses.replace(base.material, h=1e-3 * base.material.E, h_stress=1)
+    p = dataclasses.replace(base, material=mat)
+    ref0 = nw.run(dataclasses.replace(p, material=dataclasses.replace(mat, h_stress=0)), n_steps=16, energy=False)
+    ref, reac, its, kh = _curve_check(p, 16, precision=precision)
+    assert np.abs(ref["reaction"] - ref0["reaction"]).max() > 1e-4 * np.abs(ref["reaction"]).max()
+    np.testing.assert_allclose(kh, ref["state"].kappa_hist, rtol=1e-6)
+
+
 def test_bar_curve_fp32_tangent():
     """Inexact Newton with the float tangent converges to the FP64 solution."""
     p = li.bar_problem()
