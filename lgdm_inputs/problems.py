@@ -11,7 +11,7 @@ from typing import List, Optional
 
 import numpy as np
 
-from .meshes import Mesh, bar_l2, plate_q4, beam_h8, node_dofs
+from .meshes import Mesh, bar_l2, bar_l3, plate_q4, plate_q9, beam_h8, node_dofs
 
 
 @dataclass
@@ -69,34 +69,91 @@ def _bcs(pairs):
 
 def bar_problem(n: int = 100, length: float = 100.0, area: float = 10.0,
                 weak_factor: float = 0.9, u_max: float = 0.02, n_steps: int = 200,
-                material: Optional[Material] = None) -> Problem:
-    """1D bar in tension; the middle element (0-based n//2) has a weaker section."""
-    mesh = bar_l2(n, length, area)
-    mesh.vol_scale[n // 2] *= weak_factor
+                material: Optional[Material] = None, order: int = 1,
+                weak_span: Optional[tuple] = None) -> Problem:
+    """1D bar in tension.  The middle element (0-based n//2) has a weaker
+    section, or, with ``weak_span`` = (x0, x1), every element whose centre
+    lies in it.  order 1: 2-node elements for both fields; order 2: 3-node
+    quadratic u with linear micro-equivalent strain."""
+    mesh = bar_l2(n, length, area) if order == 1 else bar_l3(n, length, area)
+    if weak_span is None:
+        mesh.vol_scale[n // 2] *= weak_factor
+    else:
+        xc = (np.arange(n) + 0.5) * length / n
+        mesh.vol_scale[(xc > weak_span[0]) & (xc < weak_span[1])] *= weak_factor
     mat = material or Material(E=20000.0, nu=0.0, k=1.0, c=4.0)
-    bcs = _bcs([(node_dofs(mesh, [0], 0), 0.0), (node_dofs(mesh, [n], 0), 1.0)])
-    return Problem("bar1d", mesh, mat, bcs, u_max, n_steps)
+    right = n if order == 1 else 2 * n
+    bcs = _bcs([(node_dofs(mesh, [0], 0), 0.0), (node_dofs(mesh, [right], 0), 1.0)])
+    return Problem("bar1d" if order == 1 else "bar1d_l3", mesh, mat, bcs, u_max, n_steps)
 
 
 def sen_plate_problem(nx: int = 200, ny: int = 200, lx: float = 100.0, ly: float = 100.0,
                       notch_frac: float = 0.5, u_max: float = 0.1, n_steps: int = 500,
-                      material: Optional[Material] = None) -> Problem:
+                      material: Optional[Material] = None, order: int = 1) -> Problem:
     """Plane-strain single-edge-notched plate pulled at the top edge.
 
     Notch: element row ny//2, the first round(notch_frac*nx) elements from the
     left edge, elasticity scaled by 1e-6.  Bottom edge fixed in x and y; top
     edge u_y = load, u_x free; the micro-equivalent strain is free everywhere.
+    order 1: 4-node elements for both fields; order 2: 9-node biquadratic u
+    with bilinear micro-equivalent strain.
     """
-    mesh = plate_q4(nx, ny, lx, ly)
+    mesh = plate_q4(nx, ny, lx, ly) if order == 1 else plate_q9(nx, ny, lx, ly)
     jn = ny // 2
     nnotch = int(round(notch_frac * nx))
     mesh.e_scale[jn * nx + np.arange(nnotch)] = 1e-6
-    bottom = np.arange(nx + 1)
-    top = ny * (nx + 1) + np.arange(nx + 1)
+    row = order * nx + 1                          # nodes per grid row
+    bottom = np.arange(row)
+    top = order * ny * row + np.arange(row)
     mat = material or Material(c=1.0)
     bcs = _bcs([(node_dofs(mesh, bottom, 0), 0.0), (node_dofs(mesh, bottom, 1), 0.0),
                 (node_dofs(mesh, top, 1), 1.0)])
-    return Problem("sen_plate_q4", mesh, mat, bcs, u_max, n_steps)
+    return Problem("sen_plate_q4" if order == 1 else "sen_plate_q9", mesh, mat, bcs, u_max, n_steps)
+
+
+def paper_bar_problem(n: int = 1000, n_steps: int = 1000) -> Problem:
+    """The paper's 1D bar (Sec. 3.1, Fig. 10): 3-node quadratic u, linear
+    micro-equivalent strain, E = 1 GPa, h = 1e-9 E, kappa0 = 1e-4,
+    c = 10 mm^2, alpha = 0.99, beta = 25, R = 0.005, n = 5; 0.02 mm in 1000
+    steps on 500, 800 or 1000 elements.  Length, section and defect are not
+    printed: 100 mm, 10 mm^2, and the section 0.9x over x in [49, 51] mm (a
+    fixed physical defect, so the meshes converge)."""
+    mat = Material(E=1000.0, nu=0.0, k=1.0, kappa0=1e-4, alpha=0.99, beta=25.0, R=0.005,
+                   eta=5.0, c=10.0)
+    p = bar_problem(n, 100.0, 10.0, 0.9, u_max=0.02, n_steps=n_steps, material=mat, order=2,
+                    weak_span=(49.0, 51.0))
+    p.name = "paper_bar_l3"
+    return p
+
+
+def paper_sen_plate_problem(n: int = 100, n_steps: int = 80) -> Problem:
+    """The paper's 2D side-edge-notched specimen (Sec. 3.2): 9-node
+    biquadratic u with bilinear micro-equivalent strain on n x n elements
+    (50, 100 or 120), 0.8 mm in 80 steps of 0.01 mm.  Fig. 15 (geometry and
+    parameters) is not in the text: the plate of the notched-plate workload
+    (100 mm square, half-width notch at mid-height, its material)."""
+    p = sen_plate_problem(n, n, u_max=0.8 * n_steps / 80, n_steps=n_steps, order=2)
+    p.name = "paper_sen_plate_q9"
+    return p
+
+
+def paper_sen_slab_problem(n: int = 50, nz: int = 5, thickness: float = 10.0, n_steps: int = 80) -> Problem:
+    """The paper's 3D side-edge-notched specimen (Sec. 3.3): the 2D specimen
+    extruded to 10 mm, trilinear 8-node elements for both fields, n x n x nz
+    elements (50x50x5, 80x80x5, 100x100x5), 0.8 mm in 80 steps.  Geometry
+    and parameters as the 2D reading; the bottom face is fixed in x, y, z,
+    the top face pulled in y; the notch runs through the thickness."""
+    mesh = beam_h8(n, n, nz, 100.0, 100.0, thickness)
+    nxp = n + 1
+    k, j, i = np.meshgrid(np.arange(nz + 1), [0], np.arange(nxp), indexing="ij")
+    bottom = ((k * nxp + j) * nxp + i).ravel()
+    top = bottom + n * nxp
+    kk, ii = np.meshgrid(np.arange(nz), np.arange(int(round(0.5 * n))), indexing="ij")
+    notch = ((kk * n + n // 2) * n + ii).ravel()
+    mesh.e_scale[notch] = 1e-6
+    bcs = _bcs([(node_dofs(mesh, bottom, 0), 0.0), (node_dofs(mesh, bottom, 1), 0.0),
+                (node_dofs(mesh, bottom, 2), 0.0), (node_dofs(mesh, top, 1), 1.0)])
+    return Problem("paper_sen_slab_h8", mesh, Material(c=1.0), bcs, 0.8 * n_steps / 80, n_steps)
 
 
 def tpb_beam_problem(nx: int = 200, ny: int = 40, nz: int = 40, lx: float = 200.0,

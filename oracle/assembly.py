@@ -35,14 +35,19 @@ def assemble(mesh, mat, u, kappa_hist, chunk=20000, with_tangent=True):
     return K, r
 
 
-def apply_dirichlet(K, r, dir_dof):
+def apply_dirichlet(K, r, dir_dof, mesh=None):
     """Identity rows and zero columns on constrained dofs; zero right-hand side.
 
     Newton increments vanish on Dirichlet dofs because their prescribed values
-    were already set at the start of the load step.
+    were already set at the start of the load step.  With ``mesh`` the
+    micro-equivalent-strain dofs no element interpolates (mixed order) are
+    held at zero the same way: their rows and columns are empty, so this is
+    the same as leaving them out of the system.
     """
     m = np.ones(K.shape[0])
     m[dir_dof] = 0.0
+    if mesh is not None:
+        m[el.unused_dofs(mesh)] = 0.0
     M = sp.diags(m)
     Kb = (M @ K @ M + sp.diags(1.0 - m)).tocsr()
     return Kb, r * m

@@ -55,7 +55,7 @@ def newton(problem, state, load):
     u[bcs.dir_dof] = bcs.dir_scale * load
     for it in range(1, problem.max_newton + 1):
         K, r = asm.assemble(mesh, mat, u, state.kappa_hist)
-        Kb, rb = asm.apply_dirichlet(K, r, bcs.dir_dof)
+        Kb, rb = asm.apply_dirichlet(K, r, bcs.dir_dof, mesh)
         du = spla.spsolve(Kb.tocsc(), -rb)
         if not np.all(np.isfinite(du)):
             return None, it

@@ -9,7 +9,7 @@ from oracle import element as el
 def oracle_system(mesh, mat, bcs, u, kh):
     """Oracle tangent with Dirichlet rows/columns and the matching right-hand side."""
     K, r = asm.assemble(mesh, mat, u, kh)
-    Kb, rb = asm.apply_dirichlet(K, r, bcs.dir_dof)
+    Kb, rb = asm.apply_dirichlet(K, r, bcs.dir_dof, mesh)
     return Kb.tocsr(), -rb, r
 
 
@@ -68,6 +68,7 @@ def local_rows_oracle(mesh, mat, bcs, u, kh, nodes):
                       shape=(len(rows), mesh.ndof)).tocsr()
     isdir = np.zeros(mesh.ndof, bool)
     isdir[bcs.dir_dof] = True
+    isdir[el.unused_dofs(mesh)] = True
     K = K.tolil()
     for k, row in enumerate(rows):
         if isdir[row]:
