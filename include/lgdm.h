@@ -52,7 +52,7 @@ typedef enum {
   LGDM_ERR_STATE = 7          /* call out of order                             */
 } lgdm_status;
 
-typedef enum { LGDM_L2 = 1, LGDM_Q4 = 2, LGDM_H8 = 3 } lgdm_elem;
+typedef enum { LGDM_L2 = 1, LGDM_Q4 = 2, LGDM_H8 = 3, LGDM_L3 = 4, LGDM_Q9 = 5 } lgdm_elem;
 
 /* Arithmetic of the tangent.  FP64: everything in double.  FP32_TANGENT: the
  * element tangent is computed in float and the CSR values and node-block
@@ -88,10 +88,20 @@ typedef enum {
   LGDM_FIELD_RHS = 5         /* [ndof]  -r with zeros on Dirichlet dofs          */
 } lgdm_field;
 
-/* Mesh: equal-order elements, 2 / 2x2 / 2x2x2 Gauss points (Sec. 2.2; the
- * element types of the benchmark configurations).  Local node order: bar
- * left->right; quad counter-clockwise from (-1,-1); hex bottom face
- * counter-clockwise then top face. */
+/* Mesh (Sec. 2.2).  Equal order (L2, Q4, H8): both fields on every node,
+ * 2 / 2x2 / 2x2x2 Gauss points at +-1/sqrt(3), unit weights.  Mixed order
+ * (L3, Q9; the paper's 1D and 2D discretisation): quadratic / biquadratic u
+ * on 3 / 9 nodes, linear / bilinear micro-equivalent strain on the leading
+ * 2 / 4 (vertex) nodes, 3 / 3x3 Gauss points at 0, +-sqrt(3/5) with weights
+ * 8/9, 5/9; the geometry is interpolated like u.  Local node order: bar
+ * left->right (L3: ends, then middle); quad counter-clockwise from (-1,-1)
+ * (Q9: the four corners so, then the mid-sides of the edges xi2=-1, xi1=+1,
+ * xi2=+1, xi1=-1, then the centre); hex bottom face counter-clockwise then
+ * top face.  Gauss point q sits at the rule's abscissa times the reference
+ * position of local node q (ngp = nen).  Every node carries dim+1 dofs; the
+ * micro-equivalent-strain dof of a node that is no element's vertex (mixed
+ * order) is in no equation: the library holds it at zero like a Dirichlet
+ * dof with no load and no reaction. */
 typedef struct {
   int32_t elem;               /* lgdm_elem                                        */
   int32_t nnode, nelem;

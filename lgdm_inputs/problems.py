@@ -129,10 +129,11 @@ def paper_bar_problem(n: int = 1000, n_steps: int = 1000) -> Problem:
 def paper_sen_plate_problem(n: int = 100, n_steps: int = 80) -> Problem:
     """The paper's 2D side-edge-notched specimen (Sec. 3.2): 9-node
     biquadratic u with bilinear micro-equivalent strain on n x n elements
-    (50, 100 or 120), 0.8 mm in 80 steps of 0.01 mm.  Fig. 15 (geometry and
-    parameters) is not in the text: the plate of the notched-plate workload
-    (100 mm square, half-width notch at mid-height, its material)."""
-    p = sen_plate_problem(n, n, u_max=0.8 * n_steps / 80, n_steps=n_steps, order=2)
+    (50, 100 or 120), 80 equal load steps.  Fig. 15 (geometry and parameters)
+    is not in the text: the plate of the notched-plate workload (100 mm
+    square, half-width notch at mid-height, its material), pulled to 0.02 mm
+    -- the printed 0.8 mm would put that plate's peak inside the first step."""
+    p = sen_plate_problem(n, n, u_max=0.02 * n_steps / 80, n_steps=n_steps, order=2)
     p.name = "paper_sen_plate_q9"
     return p
 
@@ -140,9 +141,9 @@ def paper_sen_plate_problem(n: int = 100, n_steps: int = 80) -> Problem:
 def paper_sen_slab_problem(n: int = 50, nz: int = 5, thickness: float = 10.0, n_steps: int = 80) -> Problem:
     """The paper's 3D side-edge-notched specimen (Sec. 3.3): the 2D specimen
     extruded to 10 mm, trilinear 8-node elements for both fields, n x n x nz
-    elements (50x50x5, 80x80x5, 100x100x5), 0.8 mm in 80 steps.  Geometry
-    and parameters as the 2D reading; the bottom face is fixed in x, y, z,
-    the top face pulled in y; the notch runs through the thickness."""
+    elements (50x50x5, 80x80x5, 100x100x5), 80 equal load steps.  Geometry,
+    parameters and load (0.02 mm) as the 2D reading; the bottom face is fixed
+    in x, y, z, the top face pulled in y; the notch runs through the thickness."""
     mesh = beam_h8(n, n, nz, 100.0, 100.0, thickness)
     nxp = n + 1
     k, j, i = np.meshgrid(np.arange(nz + 1), [0], np.arange(nxp), indexing="ij")
@@ -153,7 +154,7 @@ def paper_sen_slab_problem(n: int = 50, nz: int = 5, thickness: float = 10.0, n_
     mesh.e_scale[notch] = 1e-6
     bcs = _bcs([(node_dofs(mesh, bottom, 0), 0.0), (node_dofs(mesh, bottom, 1), 0.0),
                 (node_dofs(mesh, bottom, 2), 0.0), (node_dofs(mesh, top, 1), 1.0)])
-    return Problem("paper_sen_slab_h8", mesh, Material(c=1.0), bcs, 0.8 * n_steps / 80, n_steps)
+    return Problem("paper_sen_slab_h8", mesh, Material(c=1.0), bcs, 0.02 * n_steps / 80, n_steps)
 
 
 def tpb_beam_problem(nx: int = 200, ny: int = 40, nz: int = 40, lx: float = 200.0,

@@ -9,7 +9,8 @@ import os
 PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(PKG, "liblgdm.so")
 
-L2, Q4, H8 = 1, 2, 3
+L2, Q4, H8, L3, Q9 = 1, 2, 3, 4, 5
+NEN = {L2: 2, Q4: 4, H8: 8, L3: 3, Q9: 9}
 PREC_FP64, PREC_FP32_TANGENT = 0, 1
 PRECOND_JACOBI, PRECOND_NODE_BLOCK, PRECOND_MULTIGRID = 0, 1, 2
 FIELD_U, FIELD_KAPPA_HIST, FIELD_DAMAGE, FIELD_DELTA, FIELD_RESIDUAL, FIELD_RHS = range(6)

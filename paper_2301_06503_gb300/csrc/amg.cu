@@ -145,10 +145,19 @@ __device__ __forceinline__ void galerkin_pair(const AmgLevel &F, const AmgLevel 
     const int32_t fp = C.cmap[c];
     const int32_t a = F.pair_node[fp], pb = F.nbr_ptr[a], deg = F.nbr_ptr[a + 1] - pb;
     const TT *blk = fv + (int64_t)ND * ND * pb + (int64_t)ND * (fp - pb);
+    if (F.held) {                              // held dofs of the finer level are not prolongated
+      const int64_t ra = (int64_t)ND * a, cb = (int64_t)ND * F.nbr[fp];
 #pragma unroll
-    for (int i = 0; i < ND; ++i)
+      for (int i = 0; i < ND; ++i)
 #pragma unroll
-      for (int j = 0; j < ND; ++j) acc[i][j] += (double)blk[(int64_t)i * ND * deg + j];
+        for (int j = 0; j < ND; ++j)
+          if (!F.held[ra + i] && !F.held[cb + j]) acc[i][j] += (double)blk[(int64_t)i * ND * deg + j];
+    } else {
+#pragma unroll
+      for (int i = 0; i < ND; ++i)
+#pragma unroll
+        for (int j = 0; j < ND; ++j) acc[i][j] += (double)blk[(int64_t)i * ND * deg + j];
+    }
   }
   TT *out = static_cast<TT *>(C.vals) + (int64_t)ND * ND * pbI + (int64_t)ND * sI;
 #pragma unroll

@@ -17,8 +17,14 @@ namespace {
 
 thread_local std::string g_last_error;   // errors raised before a handle exists
 
-int nen_of(int elem) { return elem == LGDM_L2 ? 2 : elem == LGDM_Q4 ? 4 : elem == LGDM_H8 ? 8 : 0; }
-int dim_of(int elem) { return elem == LGDM_L2 ? 1 : elem == LGDM_Q4 ? 2 : elem == LGDM_H8 ? 3 : 0; }
+int nen_of(int elem) { return elem_nen(elem); }
+int dim_of(int elem) {
+  return (elem == LGDM_L2 || elem == LGDM_L3) ? 1 : (elem == LGDM_Q4 || elem == LGDM_Q9) ? 2 : elem == LGDM_H8 ? 3 : 0;
+}
+// leading local nodes that carry the micro-equivalent strain
+int nve_of(int elem) { return elem == LGDM_L3 ? 2 : elem == LGDM_Q9 ? 4 : nen_of(elem); }
+// bits per local node in a packed element-pair contribution (element << 2 LB | a << LB | b)
+int pack_bits(int nen) { return nen > 8 ? 4 : 3; }
 
 // Node adjacency (nodes sharing an element, self included, sorted) and the
 // element-to-node-pair contribution lists.
@@ -73,7 +79,8 @@ lgdm_status build_pattern(const lgdm_mesh &m, Pattern &P, bool with_contrib, std
   }
   P.npairs = (int64_t)P.nbr.size();
   if (!with_contrib) return LGDM_OK;
-  if ((int64_t)ne * 64 > INT32_MAX) {
+  const int LB = pack_bits(nen);
+  if (((int64_t)ne << (2 * LB)) > INT32_MAX) {
     err = "too many elements for the packed contribution map";
     return LGDM_ERR_INVALID_ARG;
   }
@@ -105,7 +112,7 @@ lgdm_status build_pattern(const lgdm_mesh &m, Pattern &P, bool with_contrib, std
     for (int a = 0; a < nen; ++a)
       for (int b = 0; b < nen; ++b) {
         const int32_t p = epair[((int64_t)e * nen + a) * nen + b];
-        P.pc[pos[p]++] = e * 64 + a * 8 + b;
+        P.pc[pos[p]++] = (e << (2 * LB)) | (a << LB) | b;
       }
   return LGDM_OK;
 }
@@ -403,6 +410,7 @@ void carve(lgdm_sim &s, Carver &c) {
     V0.diag_pair = s.diag_pair;
     V0.vals = s.vals_sec;
     V0.minv = s.minv;
+    V0.held = (nve_of(s.elem) < s.nen) ? s.isdir : nullptr;
   }
   s.ws_needed = c.off + 256;
 }
@@ -655,6 +663,15 @@ lgdm_status lgdm_create(const lgdm_mesh *m, const lgdm_material *mat, const lgdm
       isdir[d] = 1;
       dscale[d] = bcs->dir_scale[i];
     }
+    // mixed order: the micro-equivalent strain of a node that is no element's
+    // vertex is in no equation; it is held at zero like an unloaded Dirichlet dof
+    if (nve_of(m->elem) < s->nen) {
+      std::vector<uint8_t> vertex(s->nnode, 0);
+      for (int32_t e = 0; e < s->nel; ++e)
+        for (int a = 0; a < nve_of(m->elem); ++a) vertex[m->conn[(int64_t)e * s->nen + a]] = 1;
+      for (int32_t n = 0; n < s->nnode; ++n)
+        if (!vertex[n]) isdir[(int64_t)s->nd * n + s->dim] = 1;
+    }
     std::vector<int32_t> reac_elems, reac_idx;
     std::vector<double> reac_w;
     for (int32_t e = 0; e < s->nel; ++e) {
@@ -755,7 +772,8 @@ lgdm_status lgdm_create(const lgdm_mesh *m, const lgdm_material *mat, const lgdm
     if (e == cudaSuccess) {
       self = self_desc(s);
       kself = krylov_args(s);
-      s->self_tiles = (s->nel + batch_tile_elements(s->elem, 128) - 1) / batch_tile_elements(s->elem, 128);
+      const int epb_self = batch_tile_elements(s->elem, s->opt.precision == LGDM_PREC_FP32_TANGENT, s->mc.hterm != 0, 128);
+      s->self_tiles = (s->nel + epb_self - 1) / epb_self;
       s->self_gblocks = (s->npairs + 255) / 256;
       s->self_pblocks = (s->nnode + 127) / 128;
       prefix[1] = s->self_tiles;
@@ -1778,7 +1796,7 @@ lgdm_status lgdm_batch_create(lgdm_sim *const *sims, int32_t n, void *ws, size_t
       hk[i] = krylov_args(s);
     }
     // groups of one element type and stress variant (one element kernel each)
-    for (int elem : {LGDM_L2, LGDM_Q4, LGDM_H8})
+    for (int elem : {LGDM_L2, LGDM_Q4, LGDM_H8, LGDM_L3, LGDM_Q9})
       for (int ht = 0; ht < 2; ++ht) {
         lgdm_batch::Group g;
         g.elem = elem;
@@ -1863,7 +1881,7 @@ lgdm_status lgdm_batch_create(lgdm_sim *const *sims, int32_t n, void *ws, size_t
     for (auto &g : b->groups) {
       const int m = (int)g.members.size();
       std::vector<int64_t> tl(m + 1, 0);
-      const int epb_ = batch_tile_elements(g.elem, b->bt);
+      const int epb_ = batch_tile_elements(g.elem, b->fp32, g.hterm, b->bt);
       for (int j = 0; j < m; ++j) tl[j + 1] = tl[j] + (b->sims[g.members[j]]->nel + epb_ - 1) / epb_;
       g.tiles = tl[m];
       LGDM_BCUDA(b, cudaMemcpyAsync(g.d_tile, tl.data(), sizeof(int64_t) * (m + 1), cudaMemcpyHostToDevice, b->stream));
@@ -1897,7 +1915,7 @@ lgdm_status lgdm_batch_set_tuning(lgdm_batch *b, int32_t block_threads, int32_t 
   for (auto &g : b->groups) {
     const int m = (int)g.members.size();
     std::vector<int64_t> tl(m + 1, 0);
-    const int epb = batch_tile_elements(g.elem, b->bt);
+    const int epb = batch_tile_elements(g.elem, b->fp32, g.hterm, b->bt);
     for (int j = 0; j < m; ++j) tl[j + 1] = tl[j] + (b->sims[g.members[j]]->nel + epb - 1) / epb;
     g.tiles = tl[m];
     LGDM_BCUDA(b, cudaMemcpyAsync(g.d_tile, tl.data(), sizeof(int64_t) * (m + 1), cudaMemcpyHostToDevice, b->stream));

@@ -1,7 +1,8 @@
 // Element integration and deterministic assembly of the LGDM coupled system.
 //
 // element_kernel: one team of NEN threads per element (NEN = NGP for the
-// 2-node bar, 4-node quad and 8-node hex with 2/2x2/2x2x2 Gauss rules).
+// 2-node bar, 4-node quad and 8-node hex with 2/2x2/2x2x2 Gauss rules, and
+// for the mixed-order 3-node bar and 9-node quad with 3/3x3 rules).
 //   Phase 1: thread q evaluates Gauss point q of its element: Jacobian,
 //     shape derivatives, strain (B_u u), micro-equivalent strain and its
 //     gradient, modified von Mises equivalent strain and gradient (Eq. A.3),
@@ -132,21 +133,27 @@ constexpr int ELEM_THREADS = 128;
 
 template <int ELEM, typename TT, int BT = ELEM_THREADS, bool HT = false>
 struct ElemLayout {
-  static constexpr int DIM = Elem<ELEM>::DIM, NEN = Elem<ELEM>::NEN, NV = Elem<ELEM>::NV;
+  static constexpr int DIM = Elem<ELEM>::DIM, NEN = Elem<ELEM>::NEN, NV = Elem<ELEM>::NV, NVE = Elem<ELEM>::NVE;
+  static constexpr bool MIX = Elem<ELEM>::MIXED;
   static constexpr int ND = DIM + 1, NGP = NEN, EPB = BT / NEN;
-  // double record per Gauss point: dNdx[NEN][DIM], sig dV[NV], rho2, rho4, gbar[DIM]
-  static constexpr int RD = NEN * DIM + NV + 2 + DIM;
+  static constexpr int DE = MIX ? NVE * DIM : 0;            // micro-strain derivatives (mixed order)
+  // double record per Gauss point: dNdx[NEN][DIM], sig dV[NV], rho2, rho4, gbar[DIM] (+ dNe/dx[NVE][DIM])
+  static constexpr int RD = NEN * DIM + NV + 2 + DIM + DE;
   static constexpr int O_DN = 0, O_SIG = NEN * DIM, O_R2 = O_SIG + NV, O_R4 = O_R2 + 1, O_GB = O_R4 + 1;
+  static constexpr int O_DE = O_GB + DIM;
   // tangent record per Gauss point (TT): dNdx[NEN][DIM], z[NEN][DIM], lam', mu', s[NV], rho1, rho2, rho3,
-  // gbar[DIM]; with the h-term stress also q[NEN][DIM] and the coefficients cy, cq of its rank-one terms
-  static constexpr int RT = 2 * NEN * DIM + 2 + NV + 3 + DIM + (HT ? NEN * DIM + 2 : 0);
+  // gbar[DIM]; with the h-term stress also q[NEN][DIM] and the coefficients cy, cq of its rank-one terms;
+  // with mixed order the micro-strain derivatives dNe/dx[NVE][DIM]
+  static constexpr int RT = 2 * NEN * DIM + 2 + NV + 3 + DIM + (HT ? NEN * DIM + 2 : 0) + DE;
   static constexpr int T_DN = 0, T_Z = NEN * DIM, T_LAM = 2 * NEN * DIM, T_MU = T_LAM + 1, T_S = T_MU + 1,
                        T_R1 = T_S + NV, T_R2 = T_R1 + 1, T_R3 = T_R2 + 1, T_GB = T_R3 + 1;
   static constexpr int T_Q = T_GB + DIM, T_CY = T_Q + NEN * DIM, T_CQ = T_CY + 1;
+  static constexpr int T_DE = T_GB + DIM + (HT ? NEN * DIM + 2 : 0);
   static constexpr int RDS = (NGP * RD) | 1;                // odd stride: fewer bank conflicts
   static constexpr int RTS = (NGP * RT) | 1;
+  static constexpr int SE = MIX ? NGP * NVE * (1 + DIM) : 0;   // micro-strain shape data (mixed order)
   static constexpr size_t BYTES_D = sizeof(double) *
-      (size_t)(NGP * NEN + NGP * NEN * DIM + EPB * NEN * DIM + EPB * NEN * ND + EPB * RDS);
+      (size_t)(NGP * NEN + NGP * NEN * DIM + SE + EPB * NEN * DIM + EPB * NEN * ND + EPB * RDS);
   static constexpr size_t bytes(bool res_only) {
     return BYTES_D + (res_only ? 0 : sizeof(TT) * (size_t)(EPB * RTS));
   }
@@ -160,11 +167,14 @@ __device__ __forceinline__ void element_tile(const MeshView &m, const MatConst &
                                              int32_t n_elem, TT *__restrict__ Ke, double *__restrict__ re,
                                              int64_t tile, TT *__restrict__ Kcor = nullptr) {
   using L = ElemLayout<ELEM, TT, BT, HT>;
-  constexpr int DIM = L::DIM, NEN = L::NEN, NV = L::NV, ND = L::ND, NGP = L::NGP, EPB = L::EPB;
+  constexpr int DIM = L::DIM, NEN = L::NEN, NV = L::NV, ND = L::ND, NGP = L::NGP, EPB = L::EPB, NVE = L::NVE;
+  constexpr bool MIX = L::MIX;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double *sN = reinterpret_cast<double *>(smem_raw);            // [NGP][NEN]
   double *sdN = sN + NGP * NEN;                                  // [NGP][NEN][DIM]
-  double *xs = sdN + NGP * NEN * DIM;                            // [EPB][NEN][DIM]
+  double *sNe = sdN + NGP * NEN * DIM;                           // mixed order: [NGP][NVE]
+  double *sdNe = sNe + (MIX ? NGP * NVE : 0);                    // mixed order: [NGP][NVE][DIM]
+  double *xs = sN + NGP * NEN + NGP * NEN * DIM + L::SE;         // [EPB][NEN][DIM]
   double *us = xs + EPB * NEN * DIM;                             // [EPB][NEN][ND]
   double *recD = us + EPB * NEN * ND;                            // [EPB][RDS]
   TT *recT = reinterpret_cast<TT *>(recD + EPB * L::RDS);        // [EPB][RTS]
@@ -172,12 +182,17 @@ __device__ __forceinline__ void element_tile(const MeshView &m, const MatConst &
   const int tid = threadIdx.x;
   const int el = tid / NEN, a = tid % NEN;
   const int64_t slot = tile * EPB + el;                          // position in the element list
-  const bool valid = slot < n_elem;
+  const bool valid = el < EPB && slot < n_elem;                  // BT need not be a multiple of NEN
   const int32_t e = valid ? (elem_list ? elem_list[slot] : (int32_t)slot) : 0;
 
-  for (int k = tid; k < NGP * NEN; k += BT) sN[k] = shape_N<DIM>(k / NEN, k % NEN);
+  for (int k = tid; k < NGP * NEN; k += BT) sN[k] = shapeU_N<ELEM>(k / NEN, k % NEN);
   for (int k = tid; k < NGP * NEN * DIM; k += BT)
-    sdN[k] = shape_dN<DIM>(k / (NEN * DIM), (k / DIM) % NEN, k % DIM);
+    sdN[k] = shapeU_dN<ELEM>(k / (NEN * DIM), (k / DIM) % NEN, k % DIM);
+  if constexpr (MIX) {
+    for (int k = tid; k < NGP * NVE; k += BT) sNe[k] = shapeE_N<ELEM>(k / NVE, k % NVE);
+    for (int k = tid; k < NGP * NVE * DIM; k += BT)
+      sdNe[k] = shapeE_dN<ELEM>(k / (NVE * DIM), (k / DIM) % NVE, k % DIM);
+  }
   if (valid) {
     const int32_t node = m.conn[(int64_t)e * NEN + a];
     xs[(el * NEN + a) * DIM + 0] = m.x[node];
@@ -230,7 +245,8 @@ __device__ __forceinline__ void element_tile(const MeshView &m, const MatConst &
       Ji[1][2] = (J[0][2] * J[1][0] - J[0][0] * J[1][2]) * id;
       Ji[2][2] = (J[0][0] * J[1][1] - J[0][1] * J[1][0]) * id;
     }
-    const double dV = det * m.vol_scale[e];
+    double dV = det * m.vol_scale[e];
+    if constexpr (MIX) dV *= gp_weight<ELEM>(q);
     // physical derivatives dN_b/dx_i = sum_j dN_b/dxi_j dxi_j/dx_i
     double g[NEN][DIM];
 #pragma unroll
@@ -260,9 +276,29 @@ __device__ __forceinline__ void element_tile(const MeshView &m, const MatConst &
         eps[4] += g[b][2] * ub[0] + g[b][0] * ub[2];
         eps[5] += g[b][1] * ub[0] + g[b][0] * ub[1];
       }
-      eb += sN[q * NEN + b] * ub[DIM];
+      if constexpr (!MIX) {
+        eb += sN[q * NEN + b] * ub[DIM];
 #pragma unroll
-      for (int i = 0; i < DIM; ++i) gb[i] += g[b][i] * ub[DIM];
+        for (int i = 0; i < DIM; ++i) gb[i] += g[b][i] * ub[DIM];
+      }
+    }
+    // mixed order: the micro-equivalent strain lives on the NVE vertex nodes
+    double gE[MIX ? NVE : 1][DIM];
+    if constexpr (MIX) {
+#pragma unroll
+      for (int b = 0; b < NVE; ++b) {
+#pragma unroll
+        for (int i = 0; i < DIM; ++i) {
+          double s = 0.0;
+#pragma unroll
+          for (int j = 0; j < DIM; ++j) s += sdNe[(q * NVE + b) * DIM + j] * Ji[j][i];
+          gE[b][i] = s;
+        }
+        const double eb_b = U[b * ND + DIM];
+        eb += sNe[q * NVE + b] * eb_b;
+#pragma unroll
+        for (int i = 0; i < DIM; ++i) gb[i] += gE[b][i] * eb_b;
+      }
     }
     double deq[NV];
     const double eq = equivalent_strain<DIM>(mc, eps, deq);
@@ -313,6 +349,12 @@ __device__ __forceinline__ void element_tile(const MeshView &m, const MatConst &
     rd[L::O_R4] = hdV * (eb - eq);
 #pragma unroll
     for (int i = 0; i < DIM; ++i) rd[L::O_GB + i] = gb[i];
+    if constexpr (MIX) {
+#pragma unroll
+      for (int b = 0; b < NVE; ++b)
+#pragma unroll
+        for (int i = 0; i < DIM; ++i) rd[L::O_DE + b * DIM + i] = gE[b][i];
+    }
     if constexpr (!RES_ONLY) {
       TT *rt = recT + el * L::RTS + q * L::RT;
       const double lin = (chi ? dD : 0.0) * dV;      // D' chi dV
@@ -338,6 +380,12 @@ __device__ __forceinline__ void element_tile(const MeshView &m, const MatConst &
       rt[L::T_R3] = (TT)(mc.h * mc.c * dgi * lin);
 #pragma unroll
       for (int i = 0; i < DIM; ++i) rt[L::T_GB + i] = (TT)gb[i];
+      if constexpr (MIX) {
+#pragma unroll
+        for (int b = 0; b < NVE; ++b)
+#pragma unroll
+          for (int i = 0; i < DIM; ++i) rt[L::T_DE + b * DIM + i] = (TT)gE[b][i];
+      }
       if constexpr (HT) {
         // tangent of the h-term stress: h dV [d (x) d + psi d2 eps_eq], psi = eps_eq - ebar.
         // With Q = b2 I1^2 + cJ J2, d2 eps_eq = [d2Q / (2 sqrt Q) - dQ (x) dQ / (4 Q^1.5)] / (2k),
@@ -399,10 +447,18 @@ __device__ __forceinline__ void element_tile(const MeshView &m, const MatConst &
       BtV<DIM, double>(A, rd + L::O_SIG, t);
 #pragma unroll
       for (int i = 0; i < DIM; ++i) ru[i] += t[i];
-      double ag = 0.0;
+      if constexpr (!MIX) {
+        double ag = 0.0;
 #pragma unroll
-      for (int i = 0; i < DIM; ++i) ag += A[i] * rd[L::O_GB + i];
-      rep += sN[q * NEN + a] * rd[L::O_R4] + rd[L::O_R2] * ag;
+        for (int i = 0; i < DIM; ++i) ag += A[i] * rd[L::O_GB + i];
+        rep += sN[q * NEN + a] * rd[L::O_R4] + rd[L::O_R2] * ag;
+      } else if (a < NVE) {                        // micro-strain rows: vertex nodes only
+        const double *Ae = rd + L::O_DE + a * DIM;
+        double ag = 0.0;
+#pragma unroll
+        for (int i = 0; i < DIM; ++i) ag += Ae[i] * rd[L::O_GB + i];
+        rep += sNe[q * NVE + a] * rd[L::O_R4] + rd[L::O_R2] * ag;
+      }
     }
     double *rout = re + ((int64_t)slot * NEN + a) * ND;
 #pragma unroll
@@ -411,7 +467,10 @@ __device__ __forceinline__ void element_tile(const MeshView &m, const MatConst &
   }
   if constexpr (!RES_ONLY) {
     const TT *RT0 = recT + el * L::RTS;
-    constexpr int BC = (NEN > 4) ? 4 : NEN;     // b columns per pass (register budget)
+    constexpr int BC = (NEN <= 4) ? NEN : (NEN % 4 == 0) ? 4 : 3;   // b columns per pass (register budget)
+    // mixed order: the micro-strain shape data of row node a (zero off the vertices)
+    const bool aE = !MIX || a < NVE;
+    const int ai = aE ? a : 0;
 #pragma unroll 1
     for (int b0 = 0; b0 < NEN; b0 += BC) {
       TT acc[ND][BC][ND];
@@ -428,7 +487,16 @@ __device__ __forceinline__ void element_tile(const MeshView &m, const MatConst &
 #pragma unroll
         for (int i = 0; i < DIM; ++i) A[i] = rt[L::T_DN + a * DIM + i];
         const TT lamp = rt[L::T_LAM], mup = rt[L::T_MU];
-        const TT Na = (TT)sN[q * NEN + a];
+        TT Na, Ae[DIM];
+        if constexpr (!MIX) {
+          Na = (TT)sN[q * NEN + a];
+#pragma unroll
+          for (int i = 0; i < DIM; ++i) Ae[i] = A[i];
+        } else {
+          Na = aE ? (TT)sNe[q * NVE + ai] : (TT)0;
+#pragma unroll
+          for (int i = 0; i < DIM; ++i) Ae[i] = aE ? rt[L::T_DE + ai * DIM + i] : (TT)0;
+        }
         TT la[DIM], ma[DIM], l2m[DIM], w[DIM], fa[DIM];
         TT ag = (TT)0;
 #pragma unroll
@@ -436,8 +504,8 @@ __device__ __forceinline__ void element_tile(const MeshView &m, const MatConst &
           la[i] = lamp * A[i];
           ma[i] = mup * A[i];
           l2m[i] = la[i] + (TT)2 * ma[i];
-          fa[i] = rt[L::T_R2] * A[i];
-          ag += A[i] * rt[L::T_GB + i];
+          fa[i] = rt[L::T_R2] * Ae[i];
+          ag += Ae[i] * rt[L::T_GB + i];
         }
         BtV<DIM, TT>(A, rt + L::T_S, w);               // B_a^T (C eps) D' chi dV
         const TT ea = Na * rt[L::T_R1] + rt[L::T_R3] * ag;
@@ -458,10 +526,20 @@ __device__ __forceinline__ void element_tile(const MeshView &m, const MatConst &
           const int b = b0 + bb;
           const TT *B = rt + L::T_DN + b * DIM;
           const TT *Z = rt + L::T_Z + b * DIM;
-          const TT Nb = (TT)shape_N<DIM>(q, b);
-          TT Bv[DIM];
+          TT Nb, Bv[DIM], BvE[DIM];
 #pragma unroll
           for (int k = 0; k < DIM; ++k) Bv[k] = B[k];
+          if constexpr (!MIX) {
+            Nb = (TT)shape_N<DIM>(q, b);
+#pragma unroll
+            for (int k = 0; k < DIM; ++k) BvE[k] = Bv[k];
+          } else {
+            const bool bE = b < NVE;
+            const int bi = bE ? b : 0;
+            Nb = bE ? (TT)sNe[q * NVE + bi] : (TT)0;
+#pragma unroll
+            for (int k = 0; k < DIM; ++k) BvE[k] = bE ? rt[L::T_DE + bi * DIM + k] : (TT)0;
+          }
           // K_uu (Eq. 11a): lam' a_i b_j + mu' a_j b_i + mu' (a.b) delta_ij
 #pragma unroll
           for (int i = 0; i < DIM; ++i)
@@ -492,7 +570,7 @@ __device__ __forceinline__ void element_tile(const MeshView &m, const MatConst &
           // K_ee (Eq. 11d)
           TT s = acc[DIM][bb][DIM] + ea * Nb;
 #pragma unroll
-          for (int k = 0; k < DIM; ++k) s += fa[k] * Bv[k];
+          for (int k = 0; k < DIM; ++k) s += fa[k] * BvE[k];
           acc[DIM][bb][DIM] = s;
         }
       }
@@ -522,13 +600,16 @@ __device__ __forceinline__ void element_tile(const MeshView &m, const MatConst &
 #pragma unroll
         for (int i = 0; i < DIM; ++i) {
           A[i] = rt[L::T_DN + a * DIM + i];
-          ag += A[i] * rt[L::T_GB + i];
+          const TT Ae = MIX ? (aE ? rt[L::T_DE + ai * DIM + i] : (TT)0) : A[i];
+          ag += Ae * rt[L::T_GB + i];
         }
         BtV<DIM, TT>(A, rt + L::T_S, w);
         const TT er = rt[L::T_R3] * ag;
 #pragma unroll
         for (int b = 0; b < NEN; ++b) {
-          const TT Nb = (TT)shape_N<DIM>(q, b);
+          TT Nb;
+          if constexpr (!MIX) Nb = (TT)shape_N<DIM>(q, b);
+          else Nb = (b < NVE) ? (TT)sNe[q * NVE + (b < NVE ? b : 0)] : (TT)0;
 #pragma unroll
           for (int i = 0; i < DIM; ++i) cor[b][i] -= w[i] * Nb;
           cor[b][DIM] += er * Nb;
@@ -580,6 +661,8 @@ cudaError_t launch_element(int elem, const MeshView &m, const MatConst &mc, cons
     case LGDM_L2: LGDM_EL(LGDM_L2);
     case LGDM_Q4: LGDM_EL(LGDM_Q4);
     case LGDM_H8: LGDM_EL(LGDM_H8);
+    case LGDM_L3: LGDM_EL(LGDM_L3);
+    case LGDM_Q9: LGDM_EL(LGDM_Q9);
   }
 #undef LGDM_EL
   return cudaErrorInvalidValue;
@@ -614,11 +697,12 @@ __device__ __forceinline__ void gather_pair(const PatternView &p, const TT *__re
   TT cacc[ND];                                   // loading-indicator terms (secant = consistent - them)
 #pragma unroll
   for (int i = 0; i < ND; ++i) cacc[i] = (TT)0;
+  constexpr int LB = (NEN > 8) ? 4 : 3;          // bits per local node in the packed contribution
   const int32_t c1 = p.pc_ptr[pr + 1];
   for (int32_t c = p.pc_ptr[pr]; c < c1; ++c) {
     const int32_t pk = p.pc[c];
-    const int64_t e = pk >> 6;
-    const int al = (pk >> 3) & 7, bl = pk & 7;
+    const int64_t e = pk >> (2 * LB);
+    const int al = (pk >> LB) & ((1 << LB) - 1), bl = pk & ((1 << LB) - 1);
     const TT *blk = Ke + ((e * NEN + al) * ND) * (NEN * ND) + bl * ND;
 #pragma unroll
     for (int i = 0; i < ND; ++i)
@@ -671,6 +755,8 @@ cudaError_t launch_gather(int elem, const PatternView &p, const TT *Ke, const do
     case LGDM_L2: gather_kernel<2, 2, TT><<<grid, 256, 0, s>>>(p, Ke, re, vals, rraw, rhs); break;
     case LGDM_Q4: gather_kernel<3, 4, TT><<<grid, 256, 0, s>>>(p, Ke, re, vals, rraw, rhs); break;
     case LGDM_H8: gather_kernel<4, 8, TT><<<grid, 256, 0, s>>>(p, Ke, re, vals, rraw, rhs); break;
+    case LGDM_L3: gather_kernel<2, 3, TT><<<grid, 256, 0, s>>>(p, Ke, re, vals, rraw, rhs); break;
+    case LGDM_Q9: gather_kernel<3, 9, TT><<<grid, 256, 0, s>>>(p, Ke, re, vals, rraw, rhs); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
@@ -712,27 +798,40 @@ cudaError_t launch_set_dirichlet(double *u, const int32_t *dof, const double *sc
   return cudaGetLastError();
 }
 
+int elem_nen(int elem) {
+  switch (elem) {
+    case LGDM_L2: return 2;
+    case LGDM_Q4: return 4;
+    case LGDM_H8: return 8;
+    case LGDM_L3: return 3;
+    case LGDM_Q9: return 9;
+  }
+  return 0;
+}
+
 // History commit (Eq. A.2): kappa_hist <- max(kappa_hist, ebar at the Gauss point).
 template <int ELEM>
 __global__ void commit_kernel(MeshView m, const double *__restrict__ u, double *__restrict__ kh) {
-  constexpr int DIM = Elem<ELEM>::DIM, NEN = Elem<ELEM>::NEN, ND = DIM + 1;
+  constexpr int DIM = Elem<ELEM>::DIM, NEN = Elem<ELEM>::NEN, NVE = Elem<ELEM>::NVE, ND = DIM + 1;
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (int64_t)m.nel * NEN) return;
   const int64_t e = t / NEN;
   const int q = (int)(t % NEN);
   double eb = 0.0;
 #pragma unroll
-  for (int b = 0; b < NEN; ++b) eb += shape_N<DIM>(q, b) * u[(int64_t)m.conn[e * NEN + b] * ND + DIM];
+  for (int b = 0; b < NVE; ++b) eb += shapeE_N<ELEM>(q, b) * u[(int64_t)m.conn[e * NEN + b] * ND + DIM];
   kh[t] = fmax(kh[t], eb);
 }
 cudaError_t launch_commit(int elem, const MeshView &m, const double *u, double *kh, cudaStream_t s) {
-  const int nen = (elem == LGDM_L2) ? 2 : (elem == LGDM_Q4) ? 4 : 8;
+  const int nen = elem_nen(elem);
   const int64_t n = (int64_t)m.nel * nen;
   const int grid = (int)((n + 255) / 256);
   switch (elem) {
     case LGDM_L2: commit_kernel<LGDM_L2><<<grid, 256, 0, s>>>(m, u, kh); break;
     case LGDM_Q4: commit_kernel<LGDM_Q4><<<grid, 256, 0, s>>>(m, u, kh); break;
     case LGDM_H8: commit_kernel<LGDM_H8><<<grid, 256, 0, s>>>(m, u, kh); break;
+    case LGDM_L3: commit_kernel<LGDM_L3><<<grid, 256, 0, s>>>(m, u, kh); break;
+    case LGDM_Q9: commit_kernel<LGDM_Q9><<<grid, 256, 0, s>>>(m, u, kh); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
@@ -786,7 +885,7 @@ __global__ void chunk_sum_kernel(const double *__restrict__ x, int64_t n, int64_
 
 cudaError_t launch_energy(int elem, const MeshView &m, const MatConst &mc, const double *u, const double *kh,
                           double *psi, double *part, double *out, cudaStream_t s) {
-  const int nen = (elem == LGDM_L2) ? 2 : (elem == LGDM_Q4) ? 4 : 8;
+  const int nen = elem_nen(elem);
   const int epb = ELEM_THREADS / nen;
   const int grid = (m.nel + epb - 1) / epb;
   size_t smem = 0;
@@ -801,6 +900,8 @@ cudaError_t launch_energy(int elem, const MeshView &m, const MatConst &mc, const
     case LGDM_L2: LGDM_EN(LGDM_L2);
     case LGDM_Q4: LGDM_EN(LGDM_Q4);
     case LGDM_H8: LGDM_EN(LGDM_H8);
+    case LGDM_L3: LGDM_EN(LGDM_L3);
+    case LGDM_Q9: LGDM_EN(LGDM_Q9);
     default: return cudaErrorInvalidValue;
   }
 #undef LGDM_EN
@@ -856,7 +957,7 @@ cudaError_t launch_external_work(double *c, double dload, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-// det J at Gauss point q of element e (unit weights of the 2-point rule).
+// w_q det J at Gauss point q of element e.
 template <int ELEM>
 __device__ __forceinline__ double gp_det(const MeshView &m, int64_t e, int q) {
   constexpr int DIM = Elem<ELEM>::DIM, NEN = Elem<ELEM>::NEN;
@@ -872,13 +973,16 @@ __device__ __forceinline__ double gp_det(const MeshView &m, int64_t e, int q) {
 #pragma unroll
     for (int i = 0; i < DIM; ++i)
 #pragma unroll
-      for (int j = 0; j < DIM; ++j) J[i][j] += X[i] * shape_dN<DIM>(q, b, j);
+      for (int j = 0; j < DIM; ++j) J[i][j] += X[i] * shapeU_dN<ELEM>(q, b, j);
   }
-  if constexpr (DIM == 1) return J[0][0];
-  else if constexpr (DIM == 2) return J[0][0] * J[1][1] - J[0][1] * J[1][0];
+  double det;
+  if constexpr (DIM == 1) det = J[0][0];
+  else if constexpr (DIM == 2) det = J[0][0] * J[1][1] - J[0][1] * J[1][0];
   else
-    return J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) + J[0][1] * (J[1][2] * J[2][0] - J[1][0] * J[2][2]) +
-           J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
+    det = J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) + J[0][1] * (J[1][2] * J[2][0] - J[1][0] * J[2][2]) +
+          J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
+  if constexpr (Elem<ELEM>::MIXED) det *= gp_weight<ELEM>(q);
+  return det;
 }
 
 template <int ELEM>
@@ -896,13 +1000,15 @@ __global__ void damaged_volume_kernel(MeshView m, MatConst mc, const double *__r
 
 cudaError_t launch_damaged_volume(int elem, const MeshView &m, const MatConst &mc, const double *kh, double thr,
                                   double *vol, double *part, double *out, cudaStream_t s) {
-  const int nen = (elem == LGDM_L2) ? 2 : (elem == LGDM_Q4) ? 4 : 8;
+  const int nen = elem_nen(elem);
   const int64_t n = (int64_t)m.nel * nen;
   const int grid = (int)((n + 255) / 256);
   switch (elem) {
     case LGDM_L2: damaged_volume_kernel<LGDM_L2><<<grid, 256, 0, s>>>(m, mc, kh, thr, vol); break;
     case LGDM_Q4: damaged_volume_kernel<LGDM_Q4><<<grid, 256, 0, s>>>(m, mc, kh, thr, vol); break;
     case LGDM_H8: damaged_volume_kernel<LGDM_H8><<<grid, 256, 0, s>>>(m, mc, kh, thr, vol); break;
+    case LGDM_L3: damaged_volume_kernel<LGDM_L3><<<grid, 256, 0, s>>>(m, mc, kh, thr, vol); break;
+    case LGDM_Q9: damaged_volume_kernel<LGDM_Q9><<<grid, 256, 0, s>>>(m, mc, kh, thr, vol); break;
     default: return cudaErrorInvalidValue;
   }
   cudaError_t err = cudaGetLastError();
@@ -971,13 +1077,45 @@ static cudaError_t launch_batch_element_t(const BatchSim *sims, const int32_t *m
   return cudaGetLastError();
 }
 
-int batch_tile_elements(int elem, int bt) { return bt / ((elem == LGDM_L2) ? 2 : (elem == LGDM_Q4) ? 4 : 8); }
+// Largest element block size <= bt (256, 128, 64) whose shared-memory layout
+// fits the 227 KB a block may opt in to (the FP64 8-node and 9-node layouts
+// with the h-term stress do not fit at 256 threads).
+constexpr size_t SMEM_OPTIN = 232448;
+template <int E, typename TT, bool H>
+int fit_block(int bt) {
+  while (bt > 64) {
+    const size_t b = (bt >= 256) ? ElemLayout<E, TT, 256, H>::bytes(false) : ElemLayout<E, TT, 128, H>::bytes(false);
+    if (b <= SMEM_OPTIN) return bt;
+    bt /= 2;
+  }
+  return 64;
+}
+template <typename TT, bool H>
+int fit_block_e(int elem, int bt) {
+  switch (elem) {
+    case LGDM_L2: return fit_block<LGDM_L2, TT, H>(bt);
+    case LGDM_Q4: return fit_block<LGDM_Q4, TT, H>(bt);
+    case LGDM_H8: return fit_block<LGDM_H8, TT, H>(bt);
+    case LGDM_L3: return fit_block<LGDM_L3, TT, H>(bt);
+    case LGDM_Q9: return fit_block<LGDM_Q9, TT, H>(bt);
+  }
+  return bt;
+}
+int element_block(int elem, bool fp32, bool hterm, int bt) {
+  if (fp32) return hterm ? fit_block_e<float, true>(elem, bt) : fit_block_e<float, false>(elem, bt);
+  return hterm ? fit_block_e<double, true>(elem, bt) : fit_block_e<double, false>(elem, bt);
+}
+
+int batch_tile_elements(int elem, bool fp32, bool hterm, int bt) {
+  return element_block(elem, fp32, hterm, bt) / elem_nen(elem);
+}
 
 template <typename TT>
 cudaError_t launch_batch_element(int elem, int bt, bool hterm, const BatchSim *sims, const int32_t *members,
                                  const int64_t *tile_start, int nm, int64_t total, const int32_t *active, int grid,
                                  cudaStream_t s) {
   if (total <= 0) return cudaSuccess;
+  bt = element_block(elem, sizeof(TT) == 4, hterm, bt);
 #define LGDM_BE2(E, H)                                                                                            \
   switch (bt) {                                                                                                   \
     case 64: return launch_batch_element_t<E, TT, 64, H>(sims, members, tile_start, nm, total, active, grid, s);   \
@@ -995,6 +1133,8 @@ cudaError_t launch_batch_element(int elem, int bt, bool hterm, const BatchSim *s
     case LGDM_L2: LGDM_BE(LGDM_L2);
     case LGDM_Q4: LGDM_BE(LGDM_Q4);
     case LGDM_H8: LGDM_BE(LGDM_H8);
+    case LGDM_L3: LGDM_BE(LGDM_L3);
+    case LGDM_Q9: LGDM_BE(LGDM_Q9);
   }
 #undef LGDM_BE
 #undef LGDM_BE2
@@ -1013,6 +1153,8 @@ cudaError_t launch_batch_gather(int elem, const BatchSim *sims, const int32_t *m
     case LGDM_L2: batch_gather_kernel<2, 2, TT><<<(unsigned)total_blocks, 256, 0, s>>>(sims, members, block_start, nm, active); break;
     case LGDM_Q4: batch_gather_kernel<3, 4, TT><<<(unsigned)total_blocks, 256, 0, s>>>(sims, members, block_start, nm, active); break;
     case LGDM_H8: batch_gather_kernel<4, 8, TT><<<(unsigned)total_blocks, 256, 0, s>>>(sims, members, block_start, nm, active); break;
+    case LGDM_L3: batch_gather_kernel<2, 3, TT><<<(unsigned)total_blocks, 256, 0, s>>>(sims, members, block_start, nm, active); break;
+    case LGDM_Q9: batch_gather_kernel<3, 9, TT><<<(unsigned)total_blocks, 256, 0, s>>>(sims, members, block_start, nm, active); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();

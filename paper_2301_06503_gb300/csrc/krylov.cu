@@ -226,7 +226,8 @@ __device__ __forceinline__ void lev_spmv(const AmgLevel &L, int64_t a, const dou
     if (zc) {
       const double *zb = zc + (int64_t)ND * L.agg[b];
 #pragma unroll
-      for (int j = 0; j < ND; ++j) xv[j] += vld<CG>(zb + j);
+      for (int j = 0; j < ND; ++j)
+        if (!L.held || !L.held[(int64_t)ND * b + j]) xv[j] += vld<CG>(zb + j);
     }
 #pragma unroll
     for (int i = 0; i < ND; ++i)
@@ -256,18 +257,21 @@ __device__ __forceinline__ void lev_residual(const AmgLevel &L, int64_t a, const
   for (int i = 0; i < ND; ++i) R[ND * a + i] = __ldcg(v + ND * a + i) - y[i];
 }
 
-// v_c[I] = sum of R over the members of aggregate I (fixed order); with
-// Xc given also Xc[I] = omega M_c^-1 v_c[I].
+// v_c[I] = sum of R over the members of aggregate I (fixed order; dofs the
+// finer level holds are left out); with Xc given also Xc[I] = omega M_c^-1 v_c[I].
 template <int ND, typename TT, bool CG>
-__device__ __forceinline__ void lev_restrict(const AmgLevel &C, int64_t I, const double *R, double *vc, double *Xc) {
+__device__ __forceinline__ void lev_restrict(const AmgLevel &C, int64_t I, const double *R, double *vc, double *Xc,
+                                             const uint8_t *fheld) {
   double acc[ND];
 #pragma unroll
   for (int i = 0; i < ND; ++i) acc[i] = 0.0;
   const int32_t m1 = C.mem_ptr[I + 1];
   for (int32_t m = C.mem_ptr[I]; m < m1; ++m) {
-    const double *r = R + (int64_t)ND * C.mem[m];
+    const int64_t f = (int64_t)ND * C.mem[m];
+    const double *r = R + f;
 #pragma unroll
-    for (int i = 0; i < ND; ++i) acc[i] += vld<CG>(r + i);
+    for (int i = 0; i < ND; ++i)
+      if (!fheld || !fheld[f + i]) acc[i] += vld<CG>(r + i);
   }
 #pragma unroll
   for (int i = 0; i < ND; ++i) vc[ND * I + i] = acc[i];
@@ -291,7 +295,10 @@ __device__ __forceinline__ void lev_postsmooth(const AmgLevel &L, int64_t a, con
   for (int i = 0; i < ND; ++i) r[i] = __ldcg(v + ND * a + i) - y[i];
   precond_apply<ND, TT>(static_cast<const TT *>(L.minv), a, r, out);
 #pragma unroll
-  for (int i = 0; i < ND; ++i) z[ND * a + i] = vld<CG>(X + ND * a + i) + vld<CG>(za + i) + AMG_OMEGA * out[i];
+  for (int i = 0; i < ND; ++i) {
+    const double c = (L.held && L.held[ND * a + i]) ? 0.0 : vld<CG>(za + i);
+    z[ND * a + i] = vld<CG>(X + ND * a + i) + c + AMG_OMEGA * out[i];
+  }
 }
 
 // The V-cycle below level k run by one block: vk in, zk out (levels k ..
@@ -310,7 +317,7 @@ __device__ void amg_single_block(const AmgInfo &M, int k, const double *vk, doub
     for (int64_t a = threadIdx.x; a < F.nnode; a += KT) lev_residual<ND, TT, false>(F, a, v, F.X, F.R);
     __syncthreads();
     for (int64_t I = threadIdx.x; I < C.nnode; I += KT)
-      lev_restrict<ND, TT, false>(C, I, F.R, C.v, (l + 1 < L - 1) ? C.X : nullptr);
+      lev_restrict<ND, TT, false>(C, I, F.R, C.v, (l + 1 < L - 1) ? C.X : nullptr, F.held);
     __syncthreads();
   }
   {
@@ -383,7 +390,7 @@ __device__ bool amg_apply(const KrylovArgs &A, const double *vin, double *zout, 
     if (!grid_barrier(A.bar_count, A.bar_gen, nbar, A.wait_ns)) return false;     // R_l published
     const int64_t c0 = (int64_t)bid * C.nnode / nb, c1 = (int64_t)(bid + 1) * C.nnode / nb;
     for (int64_t I = c0 + threadIdx.x; I < c1; I += KT)
-      lev_restrict<ND, TT, true>(C, I, F.R, C.v, (l + 1 < S) ? C.X : nullptr);
+      lev_restrict<ND, TT, true>(C, I, F.R, C.v, (l + 1 < S) ? C.X : nullptr, F.held);
   }
   if (!grid_barrier(A.bar_count, A.bar_gen, nbar, A.wait_ns)) return false;       // v_S published
   if (bid == 0) amg_single_block<ND, TT>(M, S, lev[S].v, lev[S].z);

@@ -10,10 +10,16 @@
 namespace lgdm {
 
 // ---------------------------------------------------------------- element traits
+// NEN: displacement nodes (= Gauss points); NVE: the leading local nodes that
+// carry the micro-equivalent strain; MIXED: quadratic u with linear NVE-node
+// micro-equivalent strain and the 3-point rule (Sec. 2.2), else equal order
+// with the 2-point rule.
 template <int ELEM> struct Elem;
-template <> struct Elem<LGDM_L2> { static constexpr int DIM = 1, NEN = 2, NV = 1; };
-template <> struct Elem<LGDM_Q4> { static constexpr int DIM = 2, NEN = 4, NV = 3; };
-template <> struct Elem<LGDM_H8> { static constexpr int DIM = 3, NEN = 8, NV = 6; };
+template <> struct Elem<LGDM_L2> { static constexpr int DIM = 1, NEN = 2, NV = 1, NVE = 2; static constexpr bool MIXED = false; };
+template <> struct Elem<LGDM_Q4> { static constexpr int DIM = 2, NEN = 4, NV = 3, NVE = 4; static constexpr bool MIXED = false; };
+template <> struct Elem<LGDM_H8> { static constexpr int DIM = 3, NEN = 8, NV = 6, NVE = 8; static constexpr bool MIXED = false; };
+template <> struct Elem<LGDM_L3> { static constexpr int DIM = 1, NEN = 3, NV = 1, NVE = 2; static constexpr bool MIXED = true; };
+template <> struct Elem<LGDM_Q9> { static constexpr int DIM = 2, NEN = 9, NV = 3, NVE = 4; static constexpr bool MIXED = true; };
 
 // Reference node signs; the first 2 rows serve the bar, the first 4 the quad.
 __host__ __device__ constexpr int ref_sign(int a, int i) {
@@ -37,6 +43,89 @@ __host__ __device__ constexpr double shape_dN(int q, int a, int j) {
   for (int i = 0; i < DIM; ++i)
     if (i != j) v *= (ref_sign(q, i) == ref_sign(a, i)) ? GP_P : GP_M;
   return v;
+}
+
+// Quadratic elements: reference coordinate (-1, 0, 1) of local node a in
+// direction i (the 3-node bar, dim 1: ends, then middle; the 9-node quad:
+// corners as the 4-node quad, mid-sides of the edges xi2=-1, xi1=1, xi2=1,
+// xi1=-1, then the centre).
+__host__ __device__ constexpr int quad_ref(int dim, int a, int i) {
+  return (dim == 1) ? ((a < 2) ? ref_sign(a, 0) : 0)
+       : (a < 4) ? ref_sign(a, i)
+       : (a == 8) ? 0
+       : (i == 0) ? ((a == 5) ? 1 : (a == 7) ? -1 : 0)
+                  : ((a == 4) ? -1 : (a == 6) ? 1 : 0);
+}
+// 3-point rule: Gauss point q at sqrt(3/5) times the position of node q.
+constexpr double SQRT_3_5 = 0.77459666924148337704;
+// 1D Lagrange polynomial of node r in {-1, 0, 1} at t, and its derivative.
+__host__ __device__ constexpr double lagrange2(int r, double t) {
+  return (r == 0) ? 1.0 - t * t : 0.5 * t * (t + r);
+}
+__host__ __device__ constexpr double lagrange2_d(int r, double t) {
+  return (r == 0) ? -2.0 * t : t + 0.5 * r;
+}
+
+// Element-generic shape data at Gauss point q: u shape functions (and
+// geometry), micro-equivalent-strain shape functions (node a < NVE), the
+// Gauss weight.  The equal-order elements keep the closed forms above.
+template <int ELEM>
+__host__ __device__ constexpr double shapeU_N(int q, int a) {
+  constexpr int DIM = Elem<ELEM>::DIM;
+  if constexpr (!Elem<ELEM>::MIXED) {
+    return shape_N<DIM>(q, a);
+  } else {
+    double v = 1.0;
+    for (int i = 0; i < DIM; ++i) v *= lagrange2(quad_ref(DIM, a, i), SQRT_3_5 * quad_ref(DIM, q, i));
+    return v;
+  }
+}
+template <int ELEM>
+__host__ __device__ constexpr double shapeU_dN(int q, int a, int j) {
+  constexpr int DIM = Elem<ELEM>::DIM;
+  if constexpr (!Elem<ELEM>::MIXED) {
+    return shape_dN<DIM>(q, a, j);
+  } else {
+    double v = 1.0;
+    for (int i = 0; i < DIM; ++i) {
+      const double t = SQRT_3_5 * quad_ref(DIM, q, i);
+      v *= (i == j) ? lagrange2_d(quad_ref(DIM, a, i), t) : lagrange2(quad_ref(DIM, a, i), t);
+    }
+    return v;
+  }
+}
+template <int ELEM>
+__host__ __device__ constexpr double shapeE_N(int q, int a) {
+  constexpr int DIM = Elem<ELEM>::DIM;
+  if constexpr (!Elem<ELEM>::MIXED) {
+    return shape_N<DIM>(q, a);
+  } else {
+    double v = 1.0;
+    for (int i = 0; i < DIM; ++i) v *= 0.5 * (1.0 + ref_sign(a, i) * SQRT_3_5 * quad_ref(DIM, q, i));
+    return v;
+  }
+}
+template <int ELEM>
+__host__ __device__ constexpr double shapeE_dN(int q, int a, int j) {
+  constexpr int DIM = Elem<ELEM>::DIM;
+  if constexpr (!Elem<ELEM>::MIXED) {
+    return shape_dN<DIM>(q, a, j);
+  } else {
+    double v = 1.0;
+    for (int i = 0; i < DIM; ++i)
+      v *= (i == j) ? 0.5 * ref_sign(a, i) : 0.5 * (1.0 + ref_sign(a, i) * SQRT_3_5 * quad_ref(DIM, q, i));
+    return v;
+  }
+}
+template <int ELEM>
+__host__ __device__ constexpr double gp_weight(int q) {
+  if constexpr (!Elem<ELEM>::MIXED) {
+    return 1.0;
+  } else {
+    double w = 1.0;
+    for (int i = 0; i < Elem<ELEM>::DIM; ++i) w *= (quad_ref(Elem<ELEM>::DIM, q, i) == 0) ? 8.0 / 9.0 : 5.0 / 9.0;
+    return w;
+  }
 }
 
 // ---------------------------------------------------------------- material
@@ -147,6 +236,10 @@ struct AmgLevel {
   const int32_t *cmap_ptr, *cmap;          // Galerkin map (level >= 1): [npairs+1], [npairs_{l-1}]
   const int32_t *agg;                      // node -> node of the next level (all but the coarsest)
   double *v, *X, *R, *z;                   // [nd*nnode] V-cycle vectors (level 0: X, R only)
+  // level 0 of mixed-order meshes: per-dof flag of the held (Dirichlet and
+  // uninterpolated micro-strain) dofs, which the prolongation, restriction and
+  // Galerkin product leave out; NULL elsewhere
+  const uint8_t *held;
 };
 
 struct AmgInfo {
@@ -187,7 +280,11 @@ struct BatchSim {
   // matrix (the consistent values minus them); both NULL without multigrid
   void *Kcor, *vals_sec;
 };
-int batch_tile_elements(int elem, int bt);
+// elements per tile of the batched element launch at block size bt (after
+// element_block's shared-memory fit)
+int batch_tile_elements(int elem, bool fp32, bool hterm, int bt);
+int element_block(int elem, bool fp32, bool hterm, int bt);
+int elem_nen(int elem);          // displacement nodes (= Gauss points) of an element type, 0 if unknown
 template <typename TT>
 cudaError_t launch_batch_element(int elem, int bt, bool hterm, const BatchSim *sims, const int32_t *members,
                                  const int64_t *tile_start, int nm, int64_t total, const int32_t *active, int grid,

@@ -56,7 +56,7 @@ class _MeshArgs:
                      _f64(mesh.z) if mesh.z is not None else None, _i32(mesh.conn).ravel(),
                      _f64(mesh.e_scale), _f64(mesh.vol_scale)]
         x, y, z, conn, es, vs = self.arrs
-        self.s = L.Mesh(int(mesh.elem), int(x.shape[0]), int(conn.shape[0] // {1: 2, 2: 4, 3: 8}[mesh.elem]),
+        self.s = L.Mesh(int(mesh.elem), int(x.shape[0]), int(conn.shape[0] // L.NEN[int(mesh.elem)]),
                         _p(x, C.c_double), _p(y, C.c_double), _p(z, C.c_double), _p(conn, C.c_int32),
                         _p(es, C.c_double), _p(vs, C.c_double))
 

@@ -14,7 +14,10 @@ at 40 x 8 x 8 hexahedra, first 90 of its 300 load steps, a few CPU hours),
 trace_plate_r14_30 and trace_beam_r7_40 (requests 14 and 7 of the seeded
 serving trace: a 56 x 56 notched plate, first 30 load steps, and a 42 x 8 x 8
 notched beam, first 40 load steps; the served results are compared with
-them).
+them).  paper_bar_l3_500_1000 (the paper's bar, quadratic u, 500 elements,
+all 1000 steps, ~1 CPU minute) and paper_sen_plate_q9_10_80 (the paper's 2D
+notched specimen with 9-node u, 10 x 10 elements, all 80 steps, ~15 CPU
+seconds) are part of the default set.
 The 200 x 200 plate has no displacement-controlled solution at step 32 (the
 oracle's Newton diverges there through all halvings), so its stored run
 ends at step 30.
@@ -55,6 +58,8 @@ CASES = {
     "batch_plate8_step1": lambda: ("batch_plate_problems()[8]", li.batch_plate_problems()[8], 1),
     "trace_plate_r14_30": lambda: ("serving_trace()[14].problem", li.serving_trace()[14].problem, 30),
     "trace_beam_r7_40": lambda: ("serving_trace()[7].problem", li.serving_trace()[7].problem, 40),
+    "paper_bar_l3_500_1000": lambda: ("paper_bar_problem(500, 1000)", li.paper_bar_problem(500, 1000), 1000),
+    "paper_sen_plate_q9_10_80": lambda: ("paper_sen_plate_problem(10, 80)", li.paper_sen_plate_problem(10, 80), 80),
 }
 ONLY_WHEN_NAMED = ("tpb_beam_40x8x8_90", "trace_plate_r14_30", "trace_beam_r7_40")
 

@@ -1,0 +1,154 @@
+"""Mixed-order elements on the GPU against the CPU oracle (Sec. 2.2: quadratic
+u with linear micro-equivalent strain; the paper's 1D and 2D problems).
+
+Assembly per block to 1e-12 (FP64) at random damaged states on distorted
+meshes spanning several tiles with a ragged last tile, both stress variants;
+the uninterpolated micro-strain dofs held at zero as the oracle holds them;
+the multigrid-preconditioned solve against a direct solve; load-displacement
+curves of the paper's bar (quadratic u, 500 elements, 1000 steps) and of its
+2D notched specimen (9-node u, 10 x 10, 80 steps) against stored oracle runs;
+a 9-node member in a batch bitwise equal to the same simulation alone.
+"""
+import dataclasses
+import json
+import os
+
+import numpy as np
+import pytest
+import scipy.sparse.linalg as spla
+
+import lgdm_inputs as li
+from _parity import ACCURACY, accuracy, block_errors, gpu_csr, oracle_system, vector_errors
+from oracle import element as el
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def _sim(problem, **kw):
+    from paper_2301_06503_gb300 import Sim
+    return Sim(problem.mesh, problem.material, problem.bcs, **kw)
+
+
+def _problems():
+    bar = li.bar_problem(n=97, order=2)                     # 3-node bars: tiles of 42, ragged
+    bar.mesh.x[1::2] += 0.2 * np.sin(np.arange(97))         # middle nodes off centre
+    plate = li.sen_plate_problem(9, 7, order=2)             # 63 nine-node quads: tiles of 14, ragged
+    plate.mesh.x = plate.mesh.x + 0.3 * np.sin(plate.mesh.y)
+    plate.mesh.y = plate.mesh.y + 0.1 * np.cos(plate.mesh.x)
+    return {"bar": bar, "plate": plate}
+
+
+@pytest.mark.parametrize("h_stress", [0, 1])
+@pytest.mark.parametrize("name", ["bar", "plate"])
+def test_fp64_assembly_matches_oracle(name, h_stress):
+    p = _problems()[name]
+    p = dataclasses.replace(p, material=dataclasses.replace(p.material, h_stress=h_stress))
+    u, kh = li.random_state(p.mesh, seed=7, kappa0=p.material.kappa0)
+    u[el.unused_dofs(p.mesh)] = 0.0
+    s = _sim(p)
+    s.set_state(u, kh)
+    s.assemble()
+    K, rhs = gpu_csr(s)
+    Kref, rref, rraw = oracle_system(p.mesh, p.material, p.bcs, u, kh)
+    eb = block_errors(p.mesh, K, Kref)
+    ev = vector_errors(p.mesh, rhs, rref)
+    assert max(eb.values()) <= 1e-12, eb
+    assert max(ev.values()) <= 1e-12, ev
+    ev = vector_errors(p.mesh, s.field("residual"), rraw)
+    assert max(ev.values()) <= 1e-12, ev
+    # the held micro-strain dofs: identity rows and zero columns on both sides
+    unused = el.unused_dofs(p.mesh)
+    assert len(unused) > 0
+    np.testing.assert_array_equal(K[unused][:, unused].toarray(), np.eye(len(unused)))
+    assert abs(K[unused]).sum() == len(unused) and abs(K[:, unused]).sum() == len(unused)
+    s.close()
+
+
+@pytest.mark.parametrize("name", ["bar", "plate"])
+def test_fp32_tangent_assembly(name):
+    p = _problems()[name]
+    u, kh = li.random_state(p.mesh, seed=8, kappa0=p.material.kappa0)
+    s = _sim(p, precision="fp32")
+    s.set_state(u, kh)
+    s.assemble()
+    K, rhs = gpu_csr(s)
+    Kref, rref, _ = oracle_system(p.mesh, p.material, p.bcs, u, kh)
+    assert max(block_errors(p.mesh, K, Kref).values()) <= 2e-6
+    assert max(vector_errors(p.mesh, rhs, rref).values()) <= 1e-12
+    s.close()
+
+
+@pytest.mark.parametrize("precond", ["multigrid", "block"])
+def test_solve_matches_direct_solve(precond):
+    """A 9-node plate (24 x 18 elements, 1 813 nodes) at an undamaged state
+    (well conditioned: random damaged states of this size defeat Krylov
+    solvers with either element order): the multigrid leaves the held dofs
+    out of its transfers; solution against the direct solve of the oracle."""
+    p = li.sen_plate_problem(24, 18, order=2)
+    u, _ = li.random_state(p.mesh, seed=21, kappa0=p.material.kappa0, strain=2e-5)
+    kh = np.full(p.mesh.nel * p.mesh.ngp, 1.0)      # far above every micro-strain: no damage
+    u[el.unused_dofs(p.mesh)] = 0.0
+    s = _sim(p, krylov_rtol=1e-12, precond=precond)
+    s.set_state(u, kh)
+    s.assemble()
+    it, rel = s.solve()
+    assert rel <= 1e-12 and it > 0
+    x = s.field("delta")
+    Kref, rref, _ = oracle_system(p.mesh, p.material, p.bcs, u, kh)
+    xref = spla.spsolve(Kref.tocsc(), rref)
+    assert np.abs(x - xref).max() <= 1e-9 * np.abs(xref).max()
+    assert np.all(x[el.unused_dofs(p.mesh)] == 0.0)
+    s.close()
+
+
+@pytest.mark.parametrize("name, precision", [("paper_bar_l3_500_1000", "fp64"),
+                                             ("paper_bar_l3_500_1000", "fp32"),
+                                             ("paper_sen_plate_q9_10_80", "fp64"),
+                                             ("paper_sen_plate_q9_10_80", "fp32")])
+def test_paper_problem_curves_against_stored_oracle(name, precision):
+    """The paper's bar (Sec. 3.1: quadratic u, linear micro-strain, its
+    parameter table, 500 elements, 0.02 mm in 1000 steps) and its 2D notched
+    specimen (Sec. 3.2: 9-node u, 4-node micro-strain, 10 x 10 elements, 80
+    steps) through the peak and the softening branch."""
+    g = json.load(open(os.path.join(GOLDEN, name + ".json")))
+    p = {"paper_bar_l3_500_1000": lambda: li.paper_bar_problem(500, 1000),
+         "paper_sen_plate_q9_10_80": lambda: li.paper_sen_plate_problem(10, 80)}[name]()
+    assert g["problem"].endswith(p.name.replace("paper_bar_l3", "paper_bar_problem(500, 1000)")
+                                 .replace("paper_sen_plate_q9", "paper_sen_plate_problem(10, 80)"))
+    s = _sim(p, precision=precision)
+    reac, _ = s.run(g["load"])
+    dmg = s.field("damage")
+    ed, psi = s.dissipated_energy()
+    unused = el.unused_dofs(p.mesh)
+    assert np.all(s.field("u")[unused] == 0.0)
+    s.close()
+    err = accuracy(p, g, reac, psi, dmg, dissipated=ed)
+    tol = ACCURACY[precision]
+    assert all(err[k] <= tol[k] for k in err), err
+
+
+def test_batch_member_bitwise_equal_alone():
+    """A 9-node plate and a 4-node plate in one batch: each member's Newton
+    step is bitwise that of the same simulation alone."""
+    from paper_2301_06503_gb300 import Batch
+    probs = [li.sen_plate_problem(12, 12, order=2), li.sen_plate_problem(20, 20)]
+    alone = []
+    for q in probs:
+        s = _sim(q, precision="fp32")
+        s.begin_step(q.load(3))
+        s.newton_step()
+        alone.append(s.field("u"))
+        s.close()
+    st = torch.cuda.Stream()
+    sims = [_sim(q, precision="fp32", stream=st) for q in probs]
+    b = Batch(sims)
+    for s_, q in zip(sims, probs):
+        s_.begin_step(q.load(3))
+    b.newton_step()
+    for s_, ua in zip(sims, alone):
+        assert np.array_equal(s_.field("u"), ua)
+    b.close()
+    for s_ in sims:
+        s_.close()

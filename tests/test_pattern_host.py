@@ -106,3 +106,15 @@ def test_empty_and_degenerate_meshes():
     with pytest.raises(_lib.LgdmError) as ei:
         pattern_counts(spare)
     assert "belongs to no element" in str(ei.value)
+
+
+@pytest.mark.parametrize("mesh", [lambda: li.bar_problem(n=7, order=2).mesh,
+                                  lambda: li.sen_plate_problem(5, 4, order=2).mesh])
+def test_mixed_order_pattern_against_brute_force(mesh):
+    """3-node bars and 9-node quads: every node pair sharing an element,
+    mid-side and centre nodes included (their micro-strain dof is held)."""
+    from paper_2301_06503_gb300.sim import pattern_counts
+    m = mesh()
+    npairs, nnz = pattern_counts(m)
+    assert npairs == _brute_pairs(m.conn)
+    assert nnz == m.nd * m.nd * npairs
