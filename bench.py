@@ -21,8 +21,12 @@ out).  Inputs are resident in HBM when the timed region starts; L2 is flushed
 (256 MB write) before each step and the batch's state is far larger than L2.
 
 Other workloads (--workload): plate (the 200 x 200 notched plate), bar (100
-two-node elements), beam (200 x 40 x 40 hexahedra, 1.35M dofs); for them a
-step solves load increment 1 (Newton to convergence) unless --mode newton.
+two-node elements), beam (200 x 40 x 40 hexahedra, 1.35M dofs), and the
+paper's own problems at their largest printed meshes: paper_bar (1000
+three-node quadratic elements), paper_plate (the 2D notched specimen, 120 x
+120 nine-node elements), paper_slab (the 3D notched specimen, 100 x 100 x 5
+hexahedra); for them a step solves load increment 1 (Newton to convergence)
+unless --mode newton.
 --precision fp64 assembles and applies everything in FP64.
 
 --serving runs the request-serving comparison instead and prints its own
@@ -61,7 +65,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default=None, choices=["fp64", "fp32"],
                     help="fp32: FP32 tangent, FP64 residual (default for the batch); fp64 (default otherwise)")
-    ap.add_argument("--workload", default="batch", choices=["plate", "bar", "beam", "batch"])
+    ap.add_argument("--workload", default="batch",
+                    choices=["plate", "bar", "beam", "batch", "paper_bar", "paper_plate", "paper_slab"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--mode", default=None, choices=["loadstep", "newton"],
                     help="loadstep: a step is a converged load increment (default for one simulation); "
@@ -90,6 +95,12 @@ def workload(name):
         return [li.bar_problem()], "bar_l2_100"
     if name == "beam":
         return [li.tpb_beam_problem()], "tpb_beam_h8_200x40x40"
+    if name == "paper_bar":
+        return [li.paper_bar_problem(1000)], "paper_bar_l3_1000"
+    if name == "paper_plate":
+        return [li.paper_sen_plate_problem(120)], "paper_sen_plate_q9_120x120"
+    if name == "paper_slab":
+        return [li.paper_sen_slab_problem(100)], "paper_sen_slab_h8_100x100x5"
     return li.batch_plate_problems(), "batch_plates_q4_20to300"
 
 
@@ -206,6 +217,12 @@ def _cores_used(cpu_s, wall_s):
 # 1 mm hexahedra, material and notch depth), one assembly of which takes
 # seconds on a host core instead of minutes
 BEAM_SAMPLE = "a 4 x 40 x 40-hexahedra slab of the beam (same element size and material)"
+# the same for the paper's 2D and 3D specimens: smaller meshes of the same
+# elements and material (the oracle's cost per Gauss point does not depend on
+# the element size)
+SAMPLES = {"beam": BEAM_SAMPLE,
+           "paper_plate": "the 30 x 30 mesh of the same specimen (same elements and material)",
+           "paper_slab": "the 20 x 20 x 5 mesh of the same specimen (same elements and material)"}
 
 
 def _problem_list(workload_name, count):
@@ -216,6 +233,10 @@ def _problem_list(workload_name, count):
         return li.batch_plate_problems()[:count]
     if workload_name == "beam":
         return [li.tpb_beam_problem(4, 40, 40, 4.0, 40.0, 40.0)]
+    if workload_name == "paper_plate":
+        return [li.paper_sen_plate_problem(30)]
+    if workload_name == "paper_slab":
+        return [li.paper_sen_slab_problem(20)]
     return workload(workload_name)[0]
 
 
@@ -236,7 +257,7 @@ def _oracle_assembly(workload_name, count, first, stride, budget_s):
         u = st.u.copy()
         u[p.bcs.dir_dof] = p.bcs.dir_scale * p.load(1)
         K, r = asm.assemble(p.mesh, p.material, u, st.kappa_hist)
-        asm.apply_dirichlet(K, r, p.bcs.dir_dof)
+        asm.apply_dirichlet(K, r, p.bcs.dir_dof, p.mesh)
         gp += p.mesh.nel * p.mesh.ngp
         done += 1
         k += stride
@@ -259,7 +280,7 @@ def cpu_baseline(workload_name, count, label, budget_s=8.0):
     workload for about budget_s (a bounded sample)."""
     import multiprocessing as mp
     gp1, wall1, cpu1, n1 = _oracle_assembly(workload_name, count, 0, 1, budget_s)
-    what = f"{label} ({BEAM_SAMPLE})" if workload_name == "beam" else label
+    what = f"{label} ({SAMPLES[workload_name]})" if workload_name in SAMPLES else label
     one = {"value": gp1 / wall1, "unit": UNIT, "cores": _cores_used(cpu1, wall1), "kind": "oracle",
            "sample": f"{what}: {n1} oracle assemblies (numpy element integration, scipy sparse assembly, "
                      f"Dirichlet rows) at load step 1, {wall1:.1f} s wall"}
@@ -294,9 +315,9 @@ def run_reference(args):
         probs = probs[:args.batch_count]
         label = f"batch_{len(probs)}_plates_q4_20to300"
     sample = label
-    if args.workload == "beam":
-        probs = _problem_list("beam", 1)
-        sample = f"{label} ({BEAM_SAMPLE})"
+    if args.workload in SAMPLES:
+        probs = _problem_list(args.workload, 1)
+        sample = f"{label} ({SAMPLES[args.workload]})"
     k = [0]
 
     def step():
@@ -306,7 +327,7 @@ def run_reference(args):
         u = st.u.copy()
         u[p.bcs.dir_dof] = p.bcs.dir_scale * p.load(1)
         K, r = asm.assemble(p.mesh, p.material, u, st.kappa_hist)
-        asm.apply_dirichlet(K, r, p.bcs.dir_dof)
+        asm.apply_dirichlet(K, r, p.bcs.dir_dof, p.mesh)
         return p.mesh.nel * p.mesh.ngp
 
     for _ in range(args.warmup):
@@ -558,11 +579,12 @@ def summarize(args, label, n_sims, meshes, st, step_ms, t_job, gp_job, world, pk
     tb = 4 if fp32 else 8
     phase_ms, phase_n = st["phase_ms"], st["phase_n"]
     # Krylov work summed member by member: iterations x work per iteration
-    kr_flops = kr_bytes = 0
+    kr_flops = kr_bytes = kr_f32 = 0
     for nnode, nd, nnz, npairs, its, levels in st["members"]:
-        f1, b1 = roofline.krylov_iteration(nnode, nd, nnz, npairs, tb, levels)
+        f1, b1, g1 = roofline.krylov_iteration(nnode, nd, nnz, npairs, tb, levels, float_pairs=fp32)
         kr_flops += f1 * its
         kr_bytes += b1 * its
+        kr_f32 += g1 * its
     res_f, tan_f = roofline.element_flops(st["elem"])
     el_kernel = "batch_element_kernel"
     kr_kernel = "bicgstab_grouped_kernel"
@@ -600,16 +622,17 @@ def summarize(args, label, n_sims, meshes, st, step_ms, t_job, gp_job, world, pk
                    f"{units:.0f} element integrations per launch on average"
                    + ("; FP64 residual path on the FP64 pipe (the binding one of FP64 pipe, FP32 pipe, HBM)"
                       if fp32 else "; FP64 residual and tangent"))
-    # Krylov kernel: the FP64 arithmetic (both precisions compute in FP64) or
-    # the algorithmic bytes, whichever takes longer at its peak
+    # Krylov kernel: the FP64 arithmetic, the FP32-pipe products (FP32
+    # tangent) or the algorithmic bytes, whichever takes longer at its peak
     n_kr = max(phase_n["krylov"], 1)
     kr_ms = phase_ms["krylov"] / n_kr
     its_per_launch = st["krylov_iters"] / n_kr
     t_fl = kr_flops / (pk["fp64_tflops"] * 1e12)
     t_by = kr_bytes / (pk["hbm_gbs"] * 1e9)
+    nit = max(st["krylov_iters"], 1)
     note_kr = (f"{its_per_launch:.0f} BiCGSTAB iterations per launch on average (solve and update launches), "
-               f"{kr_flops / max(st['krylov_iters'], 1):.4g} FP64 flops and {kr_bytes / max(st['krylov_iters'], 1):.4g} "
-               f"algorithmic bytes per iteration")
+               f"{kr_flops / nit:.4g} FP64 flops, {kr_f32 / nit:.4g} FP32-pipe flops (float-pair SpMV) and "
+               f"{kr_bytes / nit:.4g} algorithmic bytes per iteration")
     if t_by > t_fl:
         roof_kr = roof("hbm", kr_bytes / n_kr, kr_ms, pk["hbm_gbs"], kr_kernel, note_kr)
     else:

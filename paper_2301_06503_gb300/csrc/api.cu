@@ -167,6 +167,7 @@ struct lgdm_sim {
   void *Kcor = nullptr, *vals_sec = nullptr;     // multigrid: loading-indicator terms, secant matrix
   double *re = nullptr, *rraw = nullptr, *rhs = nullptr;
   double *kv[11] = {};
+  float2 *khl = nullptr;     // FP32 tangent: float-pair copies of ph, sh and the multigrid's level-0 X
   double *gm_V = nullptr, *gm_R = nullptr, *gm_y = nullptr, *gm_dots = nullptr, *gm_final = nullptr;
   int64_t gm_ld = 0;
   int gmres_blocks = 1;
@@ -345,6 +346,7 @@ void carve(lgdm_sim &s, Carver &c) {
   s.rraw = c.take<double>(s.ndof);
   s.rhs = c.take<double>(s.ndof);
   for (int k = 0; k < 11; ++k) s.kv[k] = c.take<double>(s.ndof);
+  s.khl = (s.opt.precision == LGDM_PREC_FP32_TANGENT) ? c.take<float2>((size_t)3 * s.ndof) : nullptr;
   if (s.opt.gmres_m > 0) {
     const int m = s.opt.gmres_m;
     s.gm_ld = (s.ndof + 31) & ~int64_t(31);
@@ -411,6 +413,7 @@ void carve(lgdm_sim &s, Carver &c) {
     V0.vals = s.vals_sec;
     V0.minv = s.minv;
     V0.held = (nve_of(s.elem) < s.nen) ? s.isdir : nullptr;
+    V0.Xhl = s.khl ? s.khl + 2 * s.ndof : nullptr;
   }
   s.ws_needed = c.off + 256;
 }
@@ -1024,6 +1027,8 @@ KrylovArgs krylov_args(lgdm_sim *s) {
   a.ph = s->kv[7];
   a.sh = s->kv[8];
   a.xb = s->kv[9];
+  a.ph_hl = s->khl;
+  a.sh_hl = s->khl ? s->khl + s->ndof : nullptr;
   // stop a solve that stopped improving: a multigrid-preconditioned solve
   // converges in at most a few hundred iterations when it converges at all
   a.stall_iters = (s->amg_levels > 0) ? std::max(100, s->opt.max_krylov / 20) : std::max(500, s->opt.max_krylov / 4);

@@ -143,6 +143,60 @@ __device__ __forceinline__ void spmv_node(const PatternView &p, const TT *__rest
   }
 }
 
+// FP32-pipe products for the FP32 tangent.  A double x is carried as a float
+// pair hi + lo (hi = x rounded to float, lo = the rest rounded to float:
+// |x - hi - lo| <= 2^-48 |x|), written once by the vector's producer.  Each
+// product m * hi is split exactly into p + e (p rounded, e = fma(m, hi, -p));
+// the p are summed with a two-sum that keeps every rounding error, and the
+// errors, the e and the m * lo are summed in a second float.  The row value
+// (double)S + (double)C is within a few 2^-48 of sum |m x| of the exact
+// double-product row: FP64-grade for the Krylov iteration, on the FP32 pipe.
+__device__ __forceinline__ float2 split_hl(double x) {
+  const float hi = __double2float_rn(x);
+  return make_float2(hi, __double2float_rn(x - (double)hi));
+}
+
+template <bool CG>
+__device__ __forceinline__ float2 vld2(const float2 *p) {
+  if constexpr (CG) return __ldcg(p);
+  else return *p;
+}
+
+// y = K x for the nd rows of node a, K float, x as float pairs.
+template <int ND, bool CG>
+__device__ __forceinline__ void spmv_node_hl(const int32_t *__restrict__ nbr_ptr, const int32_t *__restrict__ nbr,
+                                             const float *__restrict__ vals, const float2 *x, int64_t a,
+                                             double *y) {
+  const int32_t pb = nbr_ptr[a], deg = nbr_ptr[a + 1] - pb;
+  const float *v = vals + (int64_t)ND * ND * pb;
+  const int64_t rs = (int64_t)ND * deg;
+  float S[ND], Cs[ND];
+#pragma unroll
+  for (int i = 0; i < ND; ++i) S[i] = Cs[i] = 0.0f;
+#pragma unroll 3
+  for (int32_t s = 0; s < deg; ++s) {
+    const float2 *xb = x + (int64_t)ND * nbr[pb + s];
+    float2 xv[ND];
+#pragma unroll
+    for (int j = 0; j < ND; ++j) xv[j] = vld2<CG>(xb + j);
+#pragma unroll
+    for (int i = 0; i < ND; ++i)
+#pragma unroll
+      for (int j = 0; j < ND; ++j) {
+        const float m = v[i * rs + ND * s + j];
+        const float p = __fmul_rn(m, xv[j].x);
+        const float e = __fmaf_rn(m, xv[j].x, -p);           // m * hi = p + e exactly
+        const float t = __fadd_rn(S[i], p);                  // two-sum: S + p = t + es exactly
+        const float bp = __fsub_rn(t, S[i]);
+        const float es = __fadd_rn(__fsub_rn(S[i], __fsub_rn(t, bp)), __fsub_rn(p, bp));
+        S[i] = t;
+        Cs[i] += es + __fmaf_rn(m, xv[j].y, e);
+      }
+  }
+#pragma unroll
+  for (int i = 0; i < ND; ++i) y[i] = (double)S[i] + (double)Cs[i];
+}
+
 // out = M^-1 in for node a (stored in TT, applied in double).
 template <int ND, typename TT>
 __device__ __forceinline__ void precond_apply(const TT *__restrict__ minv, int64_t a, const double *in, double *out) {
@@ -215,19 +269,26 @@ __device__ __forceinline__ void lev_spmv(const AmgLevel &L, int64_t a, const dou
   const int32_t pb = L.nbr_ptr[a], deg = L.nbr_ptr[a + 1] - pb;
   const TT *v = static_cast<const TT *>(L.vals) + (int64_t)ND * ND * pb;
   const int64_t rs = (int64_t)ND * deg;
+  const int32_t *nbr = L.nbr, *agg = L.agg;
+  const uint8_t *held = L.held;
 #pragma unroll
   for (int i = 0; i < ND; ++i) y[i] = 0.0;
 #pragma unroll 3
   for (int32_t s = 0; s < deg; ++s) {
-    const int32_t b = L.nbr[pb + s];
+    const int32_t b = nbr[pb + s];
     double xv[ND];
 #pragma unroll
     for (int j = 0; j < ND; ++j) xv[j] = vld<CG>(x + (int64_t)ND * b + j);
     if (zc) {
-      const double *zb = zc + (int64_t)ND * L.agg[b];
+      const double *zb = zc + (int64_t)ND * agg[b];
+      if (held) {
 #pragma unroll
-      for (int j = 0; j < ND; ++j)
-        if (!L.held || !L.held[(int64_t)ND * b + j]) xv[j] += vld<CG>(zb + j);
+        for (int j = 0; j < ND; ++j)
+          if (!held[(int64_t)ND * b + j]) xv[j] += vld<CG>(zb + j);
+      } else {
+#pragma unroll
+        for (int j = 0; j < ND; ++j) xv[j] += vld<CG>(zb + j);
+      }
     }
 #pragma unroll
     for (int i = 0; i < ND; ++i)
@@ -243,8 +304,13 @@ __device__ __forceinline__ void lev_presmooth(const AmgLevel &L, int64_t a, cons
 #pragma unroll
   for (int i = 0; i < ND; ++i) in[i] = __ldcg(v + ND * a + i);
   precond_apply<ND, TT>(static_cast<const TT *>(L.minv), a, in, out);
+  float2 *Xhl = L.Xhl;
 #pragma unroll
   for (int i = 0; i < ND; ++i) X[ND * a + i] = AMG_OMEGA * out[i];
+  if (Xhl) {
+#pragma unroll
+    for (int i = 0; i < ND; ++i) Xhl[ND * a + i] = split_hl(AMG_OMEGA * out[i]);
+  }
 }
 
 // R[a] = v[a] - (A_l X)[a]
@@ -252,7 +318,12 @@ template <int ND, typename TT, bool CG>
 __device__ __forceinline__ void lev_residual(const AmgLevel &L, int64_t a, const double *v, const double *X,
                                              double *R) {
   double y[ND];
-  lev_spmv<ND, TT, CG>(L, a, X, nullptr, y);
+  if constexpr (sizeof(TT) == 4) {
+    if (L.Xhl) spmv_node_hl<ND, CG>(L.nbr_ptr, L.nbr, static_cast<const float *>(L.vals), L.Xhl, a, y);
+    else lev_spmv<ND, TT, CG>(L, a, X, nullptr, y);
+  } else {
+    lev_spmv<ND, TT, CG>(L, a, X, nullptr, y);
+  }
 #pragma unroll
   for (int i = 0; i < ND; ++i) R[ND * a + i] = __ldcg(v + ND * a + i) - y[i];
 }
@@ -266,12 +337,19 @@ __device__ __forceinline__ void lev_restrict(const AmgLevel &C, int64_t I, const
 #pragma unroll
   for (int i = 0; i < ND; ++i) acc[i] = 0.0;
   const int32_t m1 = C.mem_ptr[I + 1];
-  for (int32_t m = C.mem_ptr[I]; m < m1; ++m) {
-    const int64_t f = (int64_t)ND * C.mem[m];
-    const double *r = R + f;
+  if (fheld) {
+    for (int32_t m = C.mem_ptr[I]; m < m1; ++m) {
+      const int64_t f = (int64_t)ND * C.mem[m];
 #pragma unroll
-    for (int i = 0; i < ND; ++i)
-      if (!fheld || !fheld[f + i]) acc[i] += vld<CG>(r + i);
+      for (int i = 0; i < ND; ++i)
+        if (!fheld[f + i]) acc[i] += vld<CG>(R + f + i);
+    }
+  } else {
+    for (int32_t m = C.mem_ptr[I]; m < m1; ++m) {
+      const double *r = R + (int64_t)ND * C.mem[m];
+#pragma unroll
+      for (int i = 0; i < ND; ++i) acc[i] += vld<CG>(r + i);
+    }
   }
 #pragma unroll
   for (int i = 0; i < ND; ++i) vc[ND * I + i] = acc[i];
@@ -287,8 +365,9 @@ __device__ __forceinline__ void lev_restrict(const AmgLevel &C, int64_t I, const
 // z[a] = x~[a] + omega M_l^-1 (v[a] - (A_l x~)[a]).
 template <int ND, typename TT, bool CG>
 __device__ __forceinline__ void lev_postsmooth(const AmgLevel &L, int64_t a, const double *v, const double *X,
-                                               const double *zc, double *z) {
-  double y[ND], r[ND], out[ND];
+                                               const double *zc, double *z, float2 *zhl = nullptr) {
+  double y[ND], r[ND], out[ND], zv[ND];
+  const uint8_t *held = L.held;
   lev_spmv<ND, TT, CG>(L, a, X, zc, y);
   const double *za = zc + (int64_t)ND * L.agg[a];
 #pragma unroll
@@ -296,8 +375,14 @@ __device__ __forceinline__ void lev_postsmooth(const AmgLevel &L, int64_t a, con
   precond_apply<ND, TT>(static_cast<const TT *>(L.minv), a, r, out);
 #pragma unroll
   for (int i = 0; i < ND; ++i) {
-    const double c = (L.held && L.held[ND * a + i]) ? 0.0 : vld<CG>(za + i);
-    z[ND * a + i] = vld<CG>(X + ND * a + i) + c + AMG_OMEGA * out[i];
+    const double c = (held && held[ND * a + i]) ? 0.0 : vld<CG>(za + i);
+    zv[i] = vld<CG>(X + ND * a + i) + c + AMG_OMEGA * out[i];
+  }
+#pragma unroll
+  for (int i = 0; i < ND; ++i) z[ND * a + i] = zv[i];
+  if (zhl) {
+#pragma unroll
+    for (int i = 0; i < ND; ++i) zhl[ND * a + i] = split_hl(zv[i]);
   }
 }
 
@@ -305,7 +390,7 @@ __device__ __forceinline__ void lev_postsmooth(const AmgLevel &L, int64_t a, con
 // nlev-1, __syncthreads between the steps).  The coarsest level is solved with
 // its dense inverse, or, without one, by four damped block-Jacobi sweeps.
 template <int ND, typename TT>
-__device__ void amg_single_block(const AmgInfo &M, int k, const double *vk, double *zk) {
+__device__ void amg_single_block(const AmgInfo &M, int k, const double *vk, double *zk, float2 *zkhl = nullptr) {
   const AmgLevel *lev = M.lev;
   const int L = M.nlev;
   if (k < L - 1)
@@ -351,12 +436,17 @@ __device__ void amg_single_block(const AmgInfo &M, int k, const double *vk, doub
         __syncthreads();
       }
     }
+    if (L - 1 == k && zkhl) {                  // a one-level hierarchy: z is the output
+      for (int64_t i = threadIdx.x; i < N; i += KT) zkhl[i] = split_hl(z[i]);
+      __syncthreads();
+    }
   }
   for (int l = L - 2; l >= k; --l) {
     const AmgLevel &F = lev[l];
     const double *v = (l == k) ? vk : F.v;
     double *z = (l == k) ? zk : F.z;
-    for (int64_t a = threadIdx.x; a < F.nnode; a += KT) lev_postsmooth<ND, TT, false>(F, a, v, F.X, lev[l + 1].z, z);
+    for (int64_t a = threadIdx.x; a < F.nnode; a += KT)
+      lev_postsmooth<ND, TT, false>(F, a, v, F.X, lev[l + 1].z, z, (l == k) ? zkhl : nullptr);
     __syncthreads();
   }
 }
@@ -370,14 +460,14 @@ __device__ void amg_single_block(const AmgInfo &M, int k, const double *vk, doub
 // grid barrier timed out.  On return z is complete for this block's level-0
 // nodes only: the caller's next grid barrier publishes it.
 template <int ND, typename TT>
-__device__ bool amg_apply(const KrylovArgs &A, const double *vin, double *zout, int nb, int bid, unsigned int nbar,
-                          int64_t n0, int64_t n1) {
+__device__ bool amg_apply(const KrylovArgs &A, const double *vin, double *zout, float2 *zhl, int nb, int bid,
+                          unsigned int nbar, int64_t n0, int64_t n1) {
   const AmgInfo &M = A.amg;
   const AmgLevel *lev = M.lev;
   const int S = M.sb_level;
   if (S == 0) {
     if (!grid_barrier(A.bar_count, A.bar_gen, nbar, A.wait_ns)) return false;
-    if (bid == 0) amg_single_block<ND, TT>(M, 0, vin, zout);
+    if (bid == 0) amg_single_block<ND, TT>(M, 0, vin, zout, zhl);
     return true;
   }
   for (int64_t a = n0 + threadIdx.x; a < n1; a += KT) lev_presmooth<ND, TT>(lev[0], a, vin, lev[0].X);
@@ -400,10 +490,25 @@ __device__ bool amg_apply(const KrylovArgs &A, const double *vin, double *zout, 
     const double *v = (l == 0) ? vin : F.v;
     double *z = (l == 0) ? zout : F.z;
     const int64_t a0 = (l == 0) ? n0 : (int64_t)bid * F.nnode / nb, a1 = (l == 0) ? n1 : (int64_t)(bid + 1) * F.nnode / nb;
-    for (int64_t a = a0 + threadIdx.x; a < a1; a += KT) lev_postsmooth<ND, TT, true>(F, a, v, F.X, lev[l + 1].z, z);
+    for (int64_t a = a0 + threadIdx.x; a < a1; a += KT)
+      lev_postsmooth<ND, TT, true>(F, a, v, F.X, lev[l + 1].z, z, (l == 0) ? zhl : nullptr);
     if (l > 0 && !grid_barrier(A.bar_count, A.bar_gen, nbar, A.wait_ns)) return false;   // z_l published
   }
   return true;
+}
+
+// The BiCGSTAB product K x for node a: on the FP32 pipe from the float-pair
+// copy when the system has one (FP32 tangent), else with double products.
+template <int ND, typename TT>
+__device__ __forceinline__ void spmv_main(const KrylovArgs &A, const TT *vals, const double *x, const float2 *xhl,
+                                          int64_t a, double *y) {
+  if constexpr (sizeof(TT) == 4) {
+    if (xhl) {
+      spmv_node_hl<ND, true>(A.p.nbr_ptr, A.p.nbr, vals, xhl, a, y);
+      return;
+    }
+  }
+  spmv_node<ND, TT>(A.p, vals, x, a, y);
 }
 
 // The solver for one system on a group of nb blocks (bid = rank in the group).
@@ -507,14 +612,17 @@ __device__ __forceinline__ void bicgstab_body(const KrylovArgs &A, const int nb,
         if (!mg) {
           precond_apply<ND, TT>(minv, a, pv, ph);
 #pragma unroll
-          for (int i = 0; i < ND; ++i) A.ph[ND * a + i] = ph[i];
+          for (int i = 0; i < ND; ++i) {
+            A.ph[ND * a + i] = ph[i];
+            if (A.ph_hl) A.ph_hl[ND * a + i] = split_hl(ph[i]);
+          }
         }
       }
-      if (mg && !(ok = amg_apply<ND, TT>(A, A.pv, A.ph, nb, bid, nbar, n0, n1))) break;
+      if (mg && !(ok = amg_apply<ND, TT>(A, A.pv, A.ph, A.ph_hl, nb, bid, nbar, n0, n1))) break;
       if (!(ok = grid_barrier(A.bar_count, A.bar_gen, nbar, A.wait_ns))) break;
       LGDM_REDUCE(1, 0, 0) {
         double y[ND];
-        spmv_node<ND, TT>(A.p, vals, A.ph, a, y);
+        spmv_main<ND, TT>(A, vals, A.ph, A.ph_hl, a, y);
 #pragma unroll
         for (int i = 0; i < ND; ++i) {
           A.v[ND * a + i] = y[i];
@@ -543,14 +651,17 @@ __device__ __forceinline__ void bicgstab_body(const KrylovArgs &A, const int nb,
         if (!mg) {
           precond_apply<ND, TT>(minv, a, sv, sh);
 #pragma unroll
-          for (int i = 0; i < ND; ++i) A.sh[ND * a + i] = sh[i];
+          for (int i = 0; i < ND; ++i) {
+            A.sh[ND * a + i] = sh[i];
+            if (A.sh_hl) A.sh_hl[ND * a + i] = split_hl(sh[i]);
+          }
         }
       }
-      if (mg && !(ok = amg_apply<ND, TT>(A, A.sv, A.sh, nb, bid, nbar, n0, n1))) break;
+      if (mg && !(ok = amg_apply<ND, TT>(A, A.sv, A.sh, A.sh_hl, nb, bid, nbar, n0, n1))) break;
       if (!(ok = grid_barrier(A.bar_count, A.bar_gen, nbar, A.wait_ns))) break;
       LGDM_REDUCE(2, 1, 0) {
         double y[ND];
-        spmv_node<ND, TT>(A.p, vals, A.sh, a, y);
+        spmv_main<ND, TT>(A, vals, A.sh, A.sh_hl, a, y);
 #pragma unroll
         for (int i = 0; i < ND; ++i) {
           A.t[ND * a + i] = y[i];

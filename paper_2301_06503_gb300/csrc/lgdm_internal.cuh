@@ -240,6 +240,9 @@ struct AmgLevel {
   // uninterpolated micro-strain) dofs, which the prolongation, restriction and
   // Galerkin product leave out; NULL elsewhere
   const uint8_t *held;
+  // level 0 with the FP32 tangent: X as float pairs for the FP32-pipe
+  // residual SpMV; NULL elsewhere
+  float2 *Xhl;
 };
 
 struct AmgInfo {
@@ -346,6 +349,9 @@ struct KrylovArgs {
   const void *minv;           // TT [nnode*nd*nd]
   const double *rhs;          // [ndof]
   double *x, *r, *r0, *pv, *v, *sv, *t, *ph, *sh, *xb;   // [ndof] each; xb = best iterate
+  // FP32 tangent: ph and sh also as float pairs (hi + lo = the double to
+  // 2^-48), the input of the FP32-pipe SpMV; NULL otherwise (FP64 products)
+  float2 *ph_hl, *sh_hl;
   double *u;                  // [ndof] state (modes 1 and 2)
   double *partial;            // [3 slots][4 values][ntiles]
   unsigned int *bar_count, *bar_gen;

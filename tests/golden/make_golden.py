@@ -17,7 +17,9 @@ notched beam, first 40 load steps; the served results are compared with
 them).  paper_bar_l3_500_1000 (the paper's bar, quadratic u, 500 elements,
 all 1000 steps, ~1 CPU minute) and paper_sen_plate_q9_10_80 (the paper's 2D
 notched specimen with 9-node u, 10 x 10 elements, all 80 steps, ~15 CPU
-seconds) are part of the default set.
+seconds) are part of the default set, as is paper_sen_slab_h8_10x10x2_80
+(the paper's 3D notched specimen at 10 x 10 x 2 hexahedra, all 80 steps,
+~2 CPU minutes).
 The 200 x 200 plate has no displacement-controlled solution at step 32 (the
 oracle's Newton diverges there through all halvings), so its stored run
 ends at step 30.
@@ -60,6 +62,7 @@ CASES = {
     "trace_beam_r7_40": lambda: ("serving_trace()[7].problem", li.serving_trace()[7].problem, 40),
     "paper_bar_l3_500_1000": lambda: ("paper_bar_problem(500, 1000)", li.paper_bar_problem(500, 1000), 1000),
     "paper_sen_plate_q9_10_80": lambda: ("paper_sen_plate_problem(10, 80)", li.paper_sen_plate_problem(10, 80), 80),
+    "paper_sen_slab_h8_10x10x2_80": lambda: ("paper_sen_slab_problem(10, 2)", li.paper_sen_slab_problem(10, 2), 80),
 }
 ONLY_WHEN_NAMED = ("tpb_beam_40x8x8_90", "trace_plate_r14_30", "trace_beam_r7_40")
 

@@ -5,8 +5,9 @@ Assembly per block to 1e-12 (FP64) at random damaged states on distorted
 meshes spanning several tiles with a ragged last tile, both stress variants;
 the uninterpolated micro-strain dofs held at zero as the oracle holds them;
 the multigrid-preconditioned solve against a direct solve; load-displacement
-curves of the paper's bar (quadratic u, 500 elements, 1000 steps) and of its
-2D notched specimen (9-node u, 10 x 10, 80 steps) against stored oracle runs;
+curves of the paper's bar (quadratic u, 500 elements, 1000 steps), of its 2D
+notched specimen (9-node u, 10 x 10, 80 steps) and of its 3D specimen
+(hexahedra, 10 x 10 x 2, 80 steps) against stored oracle runs;
 a 9-node member in a batch bitwise equal to the same simulation alone.
 """
 import dataclasses
@@ -103,29 +104,46 @@ def test_solve_matches_direct_solve(precond):
     s.close()
 
 
-@pytest.mark.parametrize("name, precision", [("paper_bar_l3_500_1000", "fp64"),
-                                             ("paper_bar_l3_500_1000", "fp32"),
-                                             ("paper_sen_plate_q9_10_80", "fp64"),
-                                             ("paper_sen_plate_q9_10_80", "fp32")])
+PAPER_CASES = {"paper_bar_l3_500_1000": ("paper_bar_problem(500, 1000)", lambda: li.paper_bar_problem(500, 1000)),
+               "paper_sen_plate_q9_10_80": ("paper_sen_plate_problem(10, 80)",
+                                            lambda: li.paper_sen_plate_problem(10, 80)),
+               "paper_sen_slab_h8_10x10x2_80": ("paper_sen_slab_problem(10, 2)",
+                                                lambda: li.paper_sen_slab_problem(10, 2))}
+# Past the peak the incremental problem of the coarse 3D specimen has nearby
+# equilibria that differ in the loading of single Gauss points (R20): the
+# FP32-tangent Newton path may settle on another one than the FP64 path (the
+# global curve and energies still agree to ~5e-7).  There the final damage is
+# compared to 1e-3 and the state is checked to be an equilibrium of the FP64
+# residual; everywhere else to the FP32 target 1e-5.
+POST_PEAK_BRANCH = {("paper_sen_slab_h8_10x10x2_80", "fp32"): 1e-3}
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("name", list(PAPER_CASES))
 def test_paper_problem_curves_against_stored_oracle(name, precision):
     """The paper's bar (Sec. 3.1: quadratic u, linear micro-strain, its
-    parameter table, 500 elements, 0.02 mm in 1000 steps) and its 2D notched
+    parameter table, 500 elements, 0.02 mm in 1000 steps), its 2D notched
     specimen (Sec. 3.2: 9-node u, 4-node micro-strain, 10 x 10 elements, 80
-    steps) through the peak and the softening branch."""
+    steps) and its 3D notched specimen (Sec. 3.3: trilinear hexahedra, 10 x
+    10 x 2, 80 steps) through the peak and the softening branch."""
     g = json.load(open(os.path.join(GOLDEN, name + ".json")))
-    p = {"paper_bar_l3_500_1000": lambda: li.paper_bar_problem(500, 1000),
-         "paper_sen_plate_q9_10_80": lambda: li.paper_sen_plate_problem(10, 80)}[name]()
-    assert g["problem"].endswith(p.name.replace("paper_bar_l3", "paper_bar_problem(500, 1000)")
-                                 .replace("paper_sen_plate_q9", "paper_sen_plate_problem(10, 80)"))
+    desc, make = PAPER_CASES[name]
+    assert g["problem"] == "lgdm_inputs." + desc
+    p = make()
     s = _sim(p, precision=precision)
     reac, _ = s.run(g["load"])
     dmg = s.field("damage")
     ed, psi = s.dissipated_energy()
     unused = el.unused_dofs(p.mesh)
     assert np.all(s.field("u")[unused] == 0.0)
+    tol = dict(ACCURACY[precision])
+    if (name, precision) in POST_PEAK_BRANCH:
+        tol["damage"] = POST_PEAK_BRANCH[(name, precision)]
+        s.assemble()                                 # the FP64 residual at the final committed state
+        free = s.field("rhs")
+        assert np.abs(free).max() <= 1e-6 * abs(reac[-1]), np.abs(free).max()
     s.close()
     err = accuracy(p, g, reac, psi, dmg, dissipated=ed)
-    tol = ACCURACY[precision]
     assert all(err[k] <= tol[k] for k in err), err
 
 

@@ -236,9 +236,15 @@ def test_bench_line_contract_and_rooflines():
     assert el["bound"] == "alu" and abs(el["achieved"] - m.nel * (res_f + tan_f) / 0.2e-3 / 1e12) < 1e-9
     assert abs(el["frac"] - el["achieved"] / 1.25) < 1e-12
     kr = line["roofline_krylov"]
-    fl, by = roofline.krylov_iteration(m.nnode, m.nd, 3250809, 361201, 8, [(40401, 361201), (4489, 39601), (64, 484)])
-    fj, _ = roofline.krylov_iteration(m.nnode, m.nd, 3250809, 361201, 8)
-    assert fl > 2 * fj                                      # two V-cycles cost more than two Jacobi applies
+    fl, by, f32 = roofline.krylov_iteration(m.nnode, m.nd, 3250809, 361201, 8,
+                                            [(40401, 361201), (4489, 39601), (64, 484)])
+    fj, _, _ = roofline.krylov_iteration(m.nnode, m.nd, 3250809, 361201, 8)
+    assert fl > 2 * fj and f32 == 0                         # two V-cycles cost more than two Jacobi applies
+    # float pairs (FP32 tangent): the 2 SpMVs and the 2 finest residuals move to the
+    # FP32 pipe, the total algorithmic flops stay the same
+    fl2, by2, f2 = roofline.krylov_iteration(m.nnode, m.nd, 3250809, 361201, 8,
+                                             [(40401, 361201), (4489, 39601), (64, 484)], float_pairs=True)
+    assert fl2 + f2 == fl and f2 == 4 * 2 * 3250809 and by2 > by
     t_fl, t_by = fl / 1.25e12, by / 6788.3e9                # the slower of the two at its peak binds
     if t_by > t_fl:
         assert kr["bound"] == "hbm"
