@@ -184,6 +184,7 @@ struct lgdm_sim {
   // kernels, so a member computes bitwise the same alone and in a batch
   BatchSim *d_self = nullptr;
   KrylovArgs *d_kself = nullptr;
+  KrylovArgs *d_kjac = nullptr;    // with the multigrid: the same system with the block-Jacobi preconditioner
   int32_t *d_one = nullptr;            // [0] = 0 (member index), [1] = 1 (active)
   int64_t *d_prefix = nullptr;         // tiles [0, t], gather blocks [0, g], precond blocks [0, p]
   int32_t *d_gstart = nullptr;         // [0, krylov_blocks]
@@ -370,6 +371,7 @@ void carve(lgdm_sim &s, Carver &c) {
   s.h_lev.assign(L, AmgLevel{});
   s.Kcor = s.vals_sec = nullptr;
   if (L > 0) {
+    s.d_kjac = c.take<KrylovArgs>(1);
     s.Kcor = c.take<char>((size_t)s.nel * s.nen * s.nen * s.nd * s.tsize);
     s.vals_sec = c.take<char>((size_t)s.nnz * s.tsize);
     s.d_lev = c.take<AmgLevel>(L);
@@ -768,7 +770,7 @@ lgdm_status lgdm_create(const lgdm_mesh *m, const lgdm_material *mat, const lgdm
       e = e ? e : up(s->d_amg_prefix, amg_prefix.data(), sizeof(int64_t) * amg_prefix.size());
     }
     BatchSim self{};
-    KrylovArgs kself{};
+    KrylovArgs kself{}, kjac{};
     int32_t one[2] = {0, 1};
     int64_t prefix[6] = {0, 0, 0, 0, 0, 0};
     int32_t gstart[2] = {0, 0};
@@ -785,6 +787,12 @@ lgdm_status lgdm_create(const lgdm_mesh *m, const lgdm_material *mat, const lgdm
       gstart[1] = s->krylov_blocks;
       e = up(s->d_self, &self, sizeof(BatchSim));
       e = e ? e : up(s->d_kself, &kself, sizeof(KrylovArgs));
+      if (s->d_kjac) {
+        kjac = kself;
+        kjac.amg = AmgInfo{};
+        kjac.stall_iters = std::max(500, s->opt.max_krylov / 4);
+        e = e ? e : up(s->d_kjac, &kjac, sizeof(KrylovArgs));
+      }
       e = e ? e : up(s->d_one, one, sizeof(one));
       e = e ? e : up(s->d_prefix, prefix, sizeof(prefix));
       e = e ? e : up(s->d_gstart, gstart, sizeof(gstart));
@@ -1072,7 +1080,8 @@ cudaError_t set_barrier_extra(lgdm_sim *s, int v) {
   return cudaMemcpyAsync(dst, &values[v ? 1 : 0], sizeof(int32_t), cudaMemcpyHostToDevice, s->stream);
 }
 
-lgdm_status run_krylov(lgdm_sim *s, int mode, SolveResult *out) {
+lgdm_status run_krylov(lgdm_sim *s, int mode, SolveResult *out, bool jacobi = false) {
+  KrylovArgs *args = (jacobi && s->d_kjac) ? s->d_kjac : s->d_kself;
   const bool inject = s->fault == 1;
   if (inject) {                                // injected: the barrier waits for a block that never comes
     s->fault = 0;
@@ -1081,10 +1090,10 @@ lgdm_status run_krylov(lgdm_sim *s, int mode, SolveResult *out) {
   {
     PhaseTimer pt(s, 3);
     if (s->opt.precision == LGDM_PREC_FP32_TANGENT)
-      LGDM_CUDA(s, launch_bicgstab_grouped<float>(s->nd, s->d_kself, s->d_one, s->d_gstart, s->d_one + 1, 1,
+      LGDM_CUDA(s, launch_bicgstab_grouped<float>(s->nd, args, s->d_one, s->d_gstart, s->d_one + 1, 1,
                                                   s->krylov_blocks, mode, s->stream));
     else
-      LGDM_CUDA(s, launch_bicgstab_grouped<double>(s->nd, s->d_kself, s->d_one, s->d_gstart, s->d_one + 1, 1,
+      LGDM_CUDA(s, launch_bicgstab_grouped<double>(s->nd, args, s->d_one, s->d_gstart, s->d_one + 1, 1,
                                                    s->krylov_blocks, mode, s->stream));
   }
   if (inject) LGDM_CUDA(s, set_barrier_extra(s, 0));
@@ -1135,6 +1144,17 @@ lgdm_status solve_robust(lgdm_sim *s, SolveResult *out, bool with_secant_left = 
   }
   lgdm_status st = run_krylov(s, 0, out);
   if (st != LGDM_OK && st != LGDM_ERR_NONFINITE) return st;
+  if (s->d_kjac && st == LGDM_OK && out->status != 0 && out->rel_res > 1e3 * s->opt.krylov_rtol) {
+    // the multigrid V-cycle did not carry the solve (its piecewise-constant
+    // aggregates can miss soft modes, e.g. the plate bending of a thin 3D
+    // specimen): BiCGSTAB again from zero with the node-block Jacobi
+    // preconditioner of the same (secant) blocks
+    const int32_t mg_iters = out->iters;
+    st = run_krylov(s, 0, out, true);
+    out->iters += mg_iters;
+    s->last.iters = out->iters;
+    if (st != LGDM_OK && st != LGDM_ERR_NONFINITE) return st;
+  }
   if (!wants_gmres(s, st, *out, with_secant_left)) return st;
   const int32_t bicg_iters = out->iters;
   if (st == LGDM_ERR_NONFINITE)
