@@ -641,7 +641,7 @@ def summarize(args, label, n_sims, meshes, st, step_ms, t_job, gp_job, world, pk
     roof_kr["traffic"] = (tr * its_per_launch) if tr is not None else None
     roof_dom = roof_kr if phase_ms["krylov"] >= phase_ms["element"] else roof_el
 
-    # the metric (SURVEY 8(d)): Gauss points over the element-integration and
+    # the metric: Gauss points over the element-integration and
     # scatter (CSR gather with the Dirichlet rows) time inside the timed
     # region; replicas: every rank's points over the slowest rank's time
     if t_asm_job is None:
