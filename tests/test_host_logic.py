@@ -267,3 +267,49 @@ def test_bench_line_fp32_element_bound():
     line = bench.summarize(args, "x", 1, [m], st, [10.0, 10.0], 0.02, st["gp"], 1, pk, None, None, None)
     el = line["roofline_element"]
     assert el["bound"] == "alu" and el["peak"] == 1.25 and line["dtype"] == "f32-tangent/f64"
+
+
+def test_paper_workloads_and_mixed_order_work_model():
+    """The paper's problems as bench workloads (their largest printed meshes)
+    and the element work model of the mixed-order elements: the micro-strain
+    terms of a 9-node quad count on its 4 vertices only, so it costs less
+    than a 9-node equal-order count and more than a 4-node quad."""
+    import argparse
+    import bench
+    from paper_2301_06503_gb300 import roofline
+    probs, label = bench.workload("paper_plate")
+    assert label == "paper_sen_plate_q9_120x120" and probs[0].mesh.nel == 14400 and probs[0].mesh.nen == 9
+    probs, label = bench.workload("paper_slab")
+    assert label == "paper_sen_slab_h8_100x100x5" and probs[0].mesh.nel == 50000
+    probs, label = bench.workload("paper_bar")
+    assert label == "paper_bar_l3_1000" and probs[0].mesh.nel == 1000 and probs[0].mesh.nen == 3
+    for w in ("paper_plate", "paper_slab"):
+        (q,) = bench._problem_list(w, 1)                # the oracle's bounded sample: same elements
+        assert q.mesh.elem == bench.workload(w)[0][0].mesh.elem and q.mesh.nel < 14400
+    r9, t9 = roofline.element_flops(5)
+    r4, t4 = roofline.element_flops(2)
+    assert r9 + t9 > 2 * (r4 + t4)
+    # a 9-node element with every node carrying the micro-strain would cost more
+    d, n, v, ne = roofline._DIMS[5]
+    roofline._DIMS[5] = (d, n, v, n)
+    try:
+        full = sum(roofline.element_flops(5))
+    finally:
+        roofline._DIMS[5] = (d, n, v, ne)
+    assert full > r9 + t9
+    # the bench line of a 9-node run: the element roofline uses that count
+    m = bench.workload("paper_plate")[0][0].mesh
+    st = {"gp": 2 * m.nel * m.ngp, "newton": 2, "elem_integrations": 2 * m.nel, "krylov_iters": 300,
+          "halvings": 0, "launches": 40,
+          "phase_ms": {"element": 1.3, "gather": 0.2, "precond": 1.0, "krylov": 100.0, "commit": 0.1,
+                       "begin_step": 0.01},
+          "phase_n": {"element": 2, "gather": 2, "precond": 2, "krylov": 4, "commit": 1, "begin_step": 1},
+          "elements": m.nel, "elem": m.elem, "nnode": m.nnode, "nel": m.nel, "nd": m.nd,
+          "nnz": 9 * 25 * m.nnode, "npairs": 25 * m.nnode,
+          "members": [(m.nnode, m.nd, 9 * 25 * m.nnode, 25 * m.nnode, 300, [(m.nnode, 25 * m.nnode), (900, 8100)])]}
+    args = argparse.Namespace(precision="fp64", steps=1, warmup=3, mode="loadstep")
+    pk = {"hbm_gbs": 6788.3, "hbm_src": "measured", "fp64_tflops": 1.25, "fp32_tflops": 75.0}
+    line = bench.summarize(args, "paper_sen_plate_q9_120x120", 1, [m], st, [100.0], 0.1, st["gp"], 1, pk,
+                           None, None, None)
+    el = line["roofline_element"]
+    assert abs(el["achieved"] - m.nel * (r9 + t9) / 0.65e-3 / 1e12) < 1e-9

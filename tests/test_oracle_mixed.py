@@ -17,6 +17,9 @@ with linear micro-equivalent strain; the paper's 1D bar and 2D specimens).
   M7  dof structure: the micro-equivalent strain of non-vertex nodes has
       empty rows and columns and is held at zero; a linear-u field gives the
       same micro-strain residual as on the linear mesh of the vertex nodes
+  M8  the paper's bar: its Fig. 10 parameters, the closed-form compliance
+      of the elastic branch, and no damage before the defect's local strain
+      reaches kappa0 (maximum principle of the micro-strain equation)
 """
 import numpy as np
 import pytest
@@ -266,3 +269,25 @@ def test_m7_dof_structure():
     e9, e4 = r9.reshape(-1, 3)[vmap, 2], r4.reshape(-1, 3)[:, 2]
     assert np.abs(e4).max() > 0.0
     np.testing.assert_allclose(e9, e4, rtol=0, atol=1e-13 * np.abs(e4).max())
+
+
+def test_m8_paper_bar_elastic_branch_and_parameters():
+    """The paper's bar (Sec. 3.1, Fig. 10 table): before damage the reaction
+    is the load over the closed-form compliance of a 100 mm bar of section
+    10 with the 2 mm defect at 0.9 of it, 98/(10 E) + 2/(9 E), E = 1 GPa.
+    The micro-equivalent strain solves a screened-Poisson problem driven by
+    the local strain, so it never exceeds the largest local strain: no Gauss
+    point's history leaves kappa0 before the defect's local strain reaches
+    it (load = kappa0 * 9 E * compliance)."""
+    p = li.paper_bar_problem(500, 1000)
+    m = p.material
+    assert (m.E, m.kappa0, m.c, m.alpha, m.beta, m.R, m.eta) == (1000.0, 1e-4, 10.0, 0.99, 25.0, 0.005, 5.0)
+    assert m.h == 1e-9 * m.E and p.mesh.nel == 500 and p.n_steps == 1000 and p.u_max == 0.02
+    comp = 98.0 / (m.E * 10.0) + 2.0 / (m.E * 9.0)
+    out = nw.run(p, n_steps=5, energy=False)
+    np.testing.assert_allclose(out["reaction"], out["load"] / comp, rtol=1e-12)
+    onset = m.kappa0 * 9.0 * m.E * comp
+    k = int(np.floor(onset / p.load(1)))                 # last step before the local onset
+    st, _ = nw.advance(p, nw.initial_state(p), p.load(k))
+    assert np.all(st.kappa_hist == m.kappa0)
+    np.testing.assert_allclose(nw.reaction_at(p, st), p.load(k) / comp, rtol=1e-12)
